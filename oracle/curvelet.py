@@ -1,0 +1,371 @@
+"""numpy layer of the FP64 oracle: grids, spin SHT, curvelet kernels, analysis and
+synthesis, in the order and notation of arXiv:1511.05578 Sec. II-III.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py). numpy.fft serves as the library
+DFT step; everything else is written out from the paper. Arrays over an azimuthal
+index m (or n, m') are kept in centred order, position m + L - 1 for |m| < L;
+harmonic coefficients f_lm sit at l*l + l + m.
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "lib", "mw_theta", "mw_phi", "half_angles", "wigner_d_factsum", "wigner_d_lrec",
+    "risbo_matrix", "delta_matrix", "quad_weight", "sht_inverse", "sht_forward",
+    "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "psi",
+    "analysis_rings", "analysis_from_flm", "analysis", "scaling_map", "wigner_forward_Y",
+    "wigner_forward_coeffs", "synthesis_flm", "synthesis", "MUTATION",
+]
+
+# Deliberate-mistake switches, used only by tests that check the pins catch them.
+MUTATION = {"ext_sign": False, "half_phase": False, "weight_sign": False}
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        h = ctypes.CDLL(_build.build())
+        h.orc_d_factsum.restype = ctypes.c_double
+        h.orc_d_factsum.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+        h.orc_d_lrec.restype = None
+        h.orc_d_lrec.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_risbo_matrix.restype = None
+        h.orc_risbo_matrix.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_sht_fwd_contract.restype = None
+        h.orc_sht_fwd_contract.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+        h.orc_wigner_fwd_contract.restype = None
+        h.orc_wigner_fwd_contract.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp]
+        h.orc_analysis_ring.restype = None
+        h.orc_analysis_ring.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_analysis_ring_lrec.restype = None
+        h.orc_analysis_ring_lrec.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_sht_inv_rings.restype = None
+        h.orc_sht_inv_rings.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
+        h.orc_d_edge.restype = ctypes.c_double
+        h.orc_d_edge.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        h.orc_d_edge_row.restype = None
+        h.orc_d_edge_row.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_k_lambda.restype = ctypes.c_double
+        h.orc_k_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib = h
+    return _lib
+
+
+def _p(a):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+# --------------------------------------------------------------------------
+# Sampling (Sec. III-A-2, Eqs. nodes_alpha, nodes_beta, nodes_gamma; the MW
+# sphere grid uses the same colatitude rule)
+# --------------------------------------------------------------------------
+def mw_theta(L):
+    return np.pi * (2 * np.arange(L) + 1) / (2 * L - 1)
+
+
+def mw_phi(L):
+    return 2 * np.pi * np.arange(2 * L - 1) / (2 * L - 1)
+
+
+def half_angles(L, idx):
+    """(sin, cos) of beta_b / 2 for beta_b = pi (2b+1)/(2L-1); exact at b = L-1 (beta = pi)."""
+    b = np.asarray(idx, dtype=np.float64)
+    sh = np.sin(np.pi * (2 * b + 1) / (2 * (2 * L - 1)))
+    ch = np.sin(np.pi * (L - 1 - b) / (2 * L - 1))
+    return sh, ch
+
+
+# --------------------------------------------------------------------------
+# Wigner functions (Sec. II-A)
+# --------------------------------------------------------------------------
+def wigner_d_factsum(l, m, n, beta):
+    """d^l_mn(beta) by the explicit factorial sum, Eq. (wigner_sum_reln). Small l only."""
+    return lib().orc_d_factsum(int(l), int(m), int(n), float(beta))
+
+
+def wigner_d_lrec(L, m, n, beta=None, sh=None, ch=None):
+    """d^l_mn(beta) for l = 0..L-1 by the three-term l-recurrence (see orc.c)."""
+    if sh is None:
+        sh, ch = math.sin(beta / 2), math.cos(beta / 2)
+    out = np.zeros(L)
+    lib().orc_d_lrec(int(L), int(m), int(n), float(sh), float(ch), _p(out))
+    return out
+
+
+def risbo_matrix(l, beta=None, sh=None, ch=None):
+    """Full d^l(beta) matrix [m+l, n+l] by Risbo's half-integer recursion."""
+    if sh is None:
+        sh, ch = math.sin(beta / 2), math.cos(beta / 2)
+    out = np.zeros((2 * l + 1, 2 * l + 1))
+    lib().orc_risbo_matrix(int(l), float(sh), float(ch), _p(out))
+    return out
+
+
+def delta_matrix(l):
+    """Delta^l_mn = d^l_mn(pi/2) (Sec. III-A-2, after Eq. flml) as [m+l, n+l]."""
+    s = math.sqrt(0.5)
+    return risbo_matrix(l, sh=s, ch=s)
+
+
+def quad_weight(p):
+    """w(p) = int_0^pi sin(b) e^{i p b} db (Eq. gmnmp), evaluated in closed form."""
+    p = np.asarray(p)
+    w = np.zeros(p.shape, dtype=np.complex128)
+    even = (p % 2) == 0
+    w[even] = 2.0 / (1.0 - p[even].astype(np.float64) ** 2)
+    w[p == 1] = 0.5j * np.pi
+    w[p == -1] = -0.5j * np.pi
+    if MUTATION["weight_sign"]:
+        w[even & (p != 0)] *= -1.0
+    return w
+
+
+def _weight_matrix(L):
+    """Wmat[m'' + L-1, m' + L-1] = w(m'' - m') for |m''|, |m'| < L."""
+    idx = np.arange(-(L - 1), L)
+    return quad_weight(idx[:, None] - idx[None, :])
+
+
+def _ext_sign(k):
+    s = np.where(np.asarray(k) % 2 == 0, 1.0, -1.0)
+    return -s if MUTATION["ext_sign"] else s
+
+
+# --------------------------------------------------------------------------
+# Spin spherical harmonic transform on the MW grid
+# --------------------------------------------------------------------------
+def sht_inverse(flm, L, s):
+    """f(theta_t, phi_p) = sum_lm f_lm sY_lm(theta_t, phi_p), with sY_lm from
+    Eq. (spin_sphericalHarmonics) summed directly (d^l_{m,-s} by l-recurrence).
+    Returns the complex map [L][2L-1]."""
+    N = 2 * L - 1
+    flm = np.ascontiguousarray(flm[: L * L], dtype=np.complex128)
+    sh, ch = half_angles(L, np.arange(L))
+    g = np.zeros((L, N), dtype=np.complex128)
+    lib().orc_sht_inv_rings(L, int(s), _p(flm.view(np.float64)), L, _p(sh), _p(ch), _p(g.view(np.float64)))
+    # sum over m of g_m e^{i m phi_p}: an inverse DFT of length 2L-1
+    return N * np.fft.ifft(np.fft.ifftshift(g, axes=1), axis=1)
+
+
+def _theta_quadrature(Fm, L, sgn_idx):
+    """Shared steps of the exact quadrature over colatitude (Eqs. TildaFmn, Fmnmp,
+    gmnmp): given F[t, ...] on t < L, extend to t in [L, 2L-2] with sign
+    (-1)^{sgn_idx}, take the DFT over the 2L-1 samples (half-sample phase of
+    beta_b), and apply the weights w. Returns G[..., m'] centred over m'."""
+    N = 2 * L - 1
+    Fbar = np.empty((N,) + Fm.shape[1:], dtype=np.complex128)
+    Fbar[:L] = Fm
+    Fbar[L:] = _ext_sign(sgn_idx) * Fm[L - 2::-1] if L > 1 else Fm[:0]
+    Fk = np.fft.fftshift(np.fft.fft(Fbar, axis=0), axes=0) / N  # over m'' centred
+    mpp = np.arange(-(L - 1), L)
+    if not MUTATION["half_phase"]:
+        Fk = Fk * np.exp(-1j * np.pi * mpp / N).reshape((N,) + (1,) * (Fk.ndim - 1))
+    Fk = np.moveaxis(Fk, 0, -1)  # [..., m'']
+    return Fk @ _weight_matrix(L)  # sum_{m''} F_{m''} w(m'' - m')
+
+
+def sht_forward(fmap, L, s):
+    """f_lm of a band-limited spin-s map on the MW grid by the exact quadrature:
+    DFT over phi, extension over theta with (-1)^{m+s}, DFT over theta, weights,
+    then Eq. (flml)-like Delta contraction with n = -s (orc_sht_fwd_contract)."""
+    N = 2 * L - 1
+    fmap = np.asarray(fmap, dtype=np.complex128).reshape(L, N)
+    F = np.fft.fftshift(np.fft.fft(fmap, axis=1), axes=1) / N  # F[t, m]
+    m = np.arange(-(L - 1), L)
+    G = 2 * np.pi * _theta_quadrature(F, L, (m + s)[None, :])  # [m, m']
+    G = np.ascontiguousarray(G)
+    flm = np.zeros(L * L, dtype=np.complex128)
+    lib().orc_sht_fwd_contract(L, int(s), _p(G.view(np.float64)), _p(flm.view(np.float64)))
+    return flm
+
+
+# --------------------------------------------------------------------------
+# Curvelet construction (Sec. II-B)
+# --------------------------------------------------------------------------
+def k_lambda(lam, t):
+    """k_lambda(t) (Sec. II-B): normalised integral of s_lambda^2(t')/t' from t to 1."""
+    h = lib()
+    t = np.asarray(t, dtype=np.float64)
+    return np.vectorize(lambda x: h.orc_k_lambda(float(lam), float(x)), otypes=[np.float64])(t)
+
+
+def J_max(lam, L):
+    """Largest analysis scale: the smallest J with lam^J >= L (reading: the paper
+    leaves J open; this J makes the admissibility sum telescope to 1 for all l < L)."""
+    J = 0
+    while lam ** J < L * (1 - 1e-14):
+        J += 1
+    return J
+
+
+def _ceil_pow(lam, e):
+    v = lam ** e
+    r = round(v)
+    return int(r) if abs(v - r) < 1e-9 * max(1.0, v) else int(math.ceil(v))
+
+
+def band_limit(lam, j, L):
+    """Band limit L_j = min(L, ceil(lam^(j+1))) of scale j (Sec. III-A-3)."""
+    return min(L, _ceil_pow(lam, j + 1))
+
+
+def L_phi(lam, J0):
+    """Band limit of the scaling map: ceil(lam^J0)."""
+    return max(1, _ceil_pow(lam, J0))
+
+
+def kappa(lam, j, L):
+    """kappa^(j)(l) = kappa_lambda(lam^-j l) = sqrt(k(l/lam^(j+1)) - k(l/lam^j)), l < L."""
+    l = np.arange(L, dtype=np.float64)
+    v = k_lambda(lam, l / lam ** (j + 1)) - k_lambda(lam, l / lam ** j)
+    return np.sqrt(np.maximum(v, 0.0))
+
+
+def phi_scaling(lam, J0, L):
+    """sqrt(4pi/(2l+1)) Phi_l0 = sqrt(k_lambda(lam^-J0 l)) (scaling function, Sec. II-B)."""
+    l = np.arange(L, dtype=np.float64)
+    return np.sqrt(k_lambda(lam, l / lam ** J0))
+
+
+def zeta(lam, j, s, Lj):
+    """Directional component rotated to the North pole, zeta_lk = sum_n
+    d^l_kn(vartheta^j) zeta~_ln with zeta~_{l,l} = 1/sqrt2, zeta~_{l,-l} = (-1)^l/sqrt2
+    (reading delta_{l|m|} in the printed definition), vartheta^j = arccos(-s/lam^j).
+    Zero for l < |s|. Returns [Lj][2Lj-1] (real)."""
+    N = 2 * Lj - 1
+    th = math.acos(-s / lam ** j)
+    sh, ch = math.sin(th / 2), math.cos(th / 2)
+    out = np.zeros((Lj, N))
+    for l in range(abs(s), Lj):
+        if l == 0:
+            out[0, Lj - 1] = lib().orc_d_edge(0, 0, sh, ch) / math.sqrt(2)
+            continue
+        dp = np.zeros(2 * l + 1)
+        dm = np.zeros(2 * l + 1)
+        lib().orc_d_edge_row(l, 1, sh, ch, _p(dp))   # d^l_{k,l}(vartheta)
+        lib().orc_d_edge_row(l, -1, sh, ch, _p(dm))  # d^l_{k,-l}(vartheta)
+        out[l, Lj - 1 - l: Lj + l] = (dp + (-1) ** l * dm) / math.sqrt(2)
+    return out
+
+
+def psi(lam, j, s, Lj):
+    """Curvelet harmonic coefficients sPsi^(j)_ln = sqrt((2l+1)/8pi^2) kappa^(j)(l) zeta_ln
+    (Eq. wav_factorized), [Lj][2Lj-1], real."""
+    l = np.arange(Lj, dtype=np.float64)
+    fac = np.sqrt((2 * l + 1) / (8 * np.pi ** 2)) * kappa(lam, j, Lj)
+    return np.ascontiguousarray(fac[:, None] * zeta(lam, j, s, Lj))
+
+
+# --------------------------------------------------------------------------
+# Curvelet analysis (Sec. II-D-1)
+# --------------------------------------------------------------------------
+def analysis_rings(flm, lam, j, s, L, rings=None, psi_j=None, method="risbo"):
+    """W^(j)(alpha_a, beta_b, gamma_g) at the requested rings b, by direct evaluation
+    of Eq. (wav_analysis_harmonic) with D^{l*}_mn = e^{i m a} d^l_mn(b) e^{i n g};
+    d^l(beta_b) by Risbo's recursion at beta_b (method="risbo") or by the
+    l-recurrence ("lrec"). Returns complex [len(rings)][2Lj-1 (a)][2Lj-1 (g)]."""
+    Lj = band_limit(lam, j, L)
+    N = 2 * Lj - 1
+    if rings is None:
+        rings = range(Lj)
+    rings = list(rings)
+    ps = psi(lam, j, s, Lj) if psi_j is None else psi_j
+    f = np.ascontiguousarray(np.asarray(flm, dtype=np.complex128)[: Lj * Lj])
+    out = np.empty((len(rings), N, N), dtype=np.complex128)
+    X = np.empty((N, N), dtype=np.complex128)
+    for i, b in enumerate(rings):
+        sh, ch = half_angles(Lj, b)
+        fn = lib().orc_analysis_ring if method == "risbo" else lib().orc_analysis_ring_lrec
+        fn(Lj, _p(f.view(np.float64)), _p(ps), float(sh), float(ch), _p(X.view(np.float64)))
+        # sum_m sum_n X_mn e^{i m alpha_a} e^{i n gamma_g}
+        out[i] = N * N * np.fft.ifft2(np.fft.ifftshift(X))
+    return out
+
+
+def scaling_map(flm, lam, J0, L):
+    """Scaling coefficients W^Phi on the MW grid of band limit ceil(lam^J0): inverse
+    spin-0 SHT of sqrt(4pi/(2l+1)) f_lm Phi*_l0 (Eq. swav_harmonic_coeff)."""
+    Lp = L_phi(lam, J0)
+    ph = phi_scaling(lam, J0, Lp)
+    c = np.zeros(Lp * Lp, dtype=np.complex128)
+    for l in range(min(Lp, L)):
+        c[l * l: (l + 1) * (l + 1)] = ph[l] * flm[l * l: (l + 1) * (l + 1)]
+    return sht_inverse(c, Lp, 0)
+
+
+def analysis_from_flm(flm, lam, J0, s, L, rings=None):
+    J = J_max(lam, L)
+    W = {}
+    for j in range(J0, J + 1):
+        W[j] = analysis_rings(flm, lam, j, s, L, None if rings is None else rings.get(j, None))
+    return W, scaling_map(flm, lam, J0, L)
+
+
+def analysis(fmap, lam, J0, s, L, rings=None):
+    """Curvelet analysis of a map: (f_lm, {W_j}, W^Phi)."""
+    flm = sht_forward(fmap, L, s)
+    W, Wphi = analysis_from_flm(flm, lam, J0, s, L, rings)
+    return flm, W, Wphi
+
+
+# --------------------------------------------------------------------------
+# Curvelet synthesis (Sec. II-D-2) through the forward Wigner quadrature (Sec. III-A-2)
+# --------------------------------------------------------------------------
+def wigner_forward_Y(Wj, Lj):
+    """Eqs. (Fmn), (TildaFmn), (Fmnmp), (gmnmp): from W on the SO(3) grid
+    [b][a][g] to Y_{m n m'} (returned as [m][n][m'], centred)."""
+    N = 2 * Lj - 1
+    Wj = np.asarray(Wj).reshape(Lj, N, N)
+    X = np.fft.fftshift(np.fft.fft2(Wj, axes=(1, 2)), axes=(1, 2)) / (N * N)  # [b][m][n]
+    m = np.arange(-(Lj - 1), Lj)
+    Y = (2 * np.pi) ** 2 * _theta_quadrature(X, Lj, (m[:, None] + m[None, :])[None, :, :])  # [m][n][m']
+    return np.ascontiguousarray(Y)
+
+
+def wigner_forward_coeffs(Wj, Lj):
+    """Wigner coefficients (W)^l_mn of W on the grid, dense [l][m][n] (Eq. flml in
+    general-n form)."""
+    N = 2 * Lj - 1
+    Y = wigner_forward_Y(Wj, Lj)
+    wl = np.zeros((Lj, N, N), dtype=np.complex128)
+    f = np.zeros(Lj * Lj, dtype=np.complex128)
+    zero_psi = np.zeros((Lj, N))
+    lib().orc_wigner_fwd_contract(Lj, _p(Y.view(np.float64)), _p(zero_psi), _p(f.view(np.float64)), _p(wl.view(np.float64)))
+    return wl
+
+
+def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None):
+    """f_lm from curvelet and scaling coefficients, Eq. (wav_synthesis_harmonic).
+    W maps scale j -> [Lj][2Lj-1][2Lj-1]; scales missing from W contribute nothing."""
+    J = J_max(lam, L)
+    f = np.zeros(L * L, dtype=np.complex128)
+    for j in range(J0, J + 1):
+        if j not in W or (scales is not None and j not in scales):
+            continue
+        Lj = band_limit(lam, j, L)
+        Y = wigner_forward_Y(W[j], Lj)
+        ps = psi(lam, j, s, Lj)
+        part = np.zeros(Lj * Lj, dtype=np.complex128)
+        lib().orc_wigner_fwd_contract(Lj, _p(Y.view(np.float64)), _p(ps), _p(part.view(np.float64)), None)
+        f[: Lj * Lj] += part
+    if Wphi is not None:
+        Lp = L_phi(lam, J0)
+        c = sht_forward(Wphi, Lp, 0)
+        ph = phi_scaling(lam, J0, Lp)
+        for l in range(min(Lp, L)):
+            f[l * l: (l + 1) * (l + 1)] += ph[l] * c[l * l: (l + 1) * (l + 1)]
+    f[: s * s] = 0.0
+    return f
+
+
+def synthesis(W, Wphi, lam, J0, s, L):
+    """Curvelet synthesis back to the MW map (complex [L][2L-1])."""
+    return sht_inverse(synthesis_flm(W, Wphi, lam, J0, s, L), L, s)
