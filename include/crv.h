@@ -1,0 +1,160 @@
+/*
+ * crv.h - C ABI of the GB300 spherical curvelet transform library (libcrv.so).
+ *
+ * Second-generation curvelets on the sphere (Chan, Leistedt, Kitching, McEwen,
+ * arXiv:1511.05578). The library computes, on one GPU:
+ *   - the spin spherical harmonic transform on the MW equiangular grid
+ *     (f_lm = <f, sY_lm>, Sec. II-A, Eq. spin_sphericalHarmonics);
+ *   - curvelet analysis: the directional convolution of Eq. (wav_analysis) in its
+ *     harmonic form Eq. (wav_analysis_harmonic), evaluated as an inverse Wigner
+ *     transform of the coefficients of Eq. (wav_harmonic_coeff) onto the SO(3)
+ *     grid of Eqs. (nodes_alpha, nodes_beta, nodes_gamma), plus the scaling
+ *     coefficients of Eq. (analysis_scaling_harmonic);
+ *   - curvelet synthesis, Eq. (wav_synthesis_harmonic), through the forward Wigner
+ *     quadrature of Sec. III-A-2 (Eqs. Fmn, TildaFmn, Fmnmp, gmnmp, flml),
+ *     exact for band-limited signals by the admissibility of Eq. (admissibility).
+ *
+ * Conventions (all entry points):
+ *   - Band limit L: f_lm = 0 for l >= L. Spin s, |s| < L; f_lm = 0 for l < |s|.
+ *   - Harmonic coefficients f_lm: complex double (interleaved re, im), index
+ *     l*l + l + m, length L*L per map.
+ *   - Maps on the MW grid: [L][2L-1], theta_t = pi(2t+1)/(2L-1),
+ *     phi_p = 2 pi p/(2L-1). Real doubles with CRV_F_REAL, otherwise complex double.
+ *   - Scales j = J0..J, J the smallest integer with lambda^J >= L. Scale j has band
+ *     limit L_j = min(L, ceil(lambda^(j+1))) (Sec. III-A-3) and coefficients
+ *     W_j[b][a][g] on alpha_a = 2 pi a/(2L_j-1), beta_b = pi(2b+1)/(2L_j-1),
+ *     gamma_g = 2 pi g/(2L_j-1): L_j * (2L_j-1) * (2L_j-1) samples per map. Real with
+ *     CRV_F_REAL, else complex; double, or float with CRV_F_W_FP32.
+ *   - Scaling coefficients W^Phi: spin-0 map on the MW grid of band limit
+ *     L_phi = ceil(lambda^J0), [L_phi][2L_phi-1], real with CRV_F_REAL else complex,
+ *     always double.
+ *   - Batches: B maps stored back to back ([B][...]), B <= max_batch of the plan.
+ *
+ * Memory and streams: every data pointer is caller-owned DEVICE memory (cudaMalloc,
+ * or a torch tensor's data_ptr) that must stay valid until the call's work on the
+ * stream has finished. The plan owns its tables and workspace (allocated by
+ * crv_plan_create, freed by crv_plan_destroy). Calls are asynchronous on the given
+ * CUDA stream (NULL = legacy default stream); only crv_plan_create and
+ * crv_plan_destroy synchronise. A plan may be used by one stream at a time. No C++
+ * exception crosses this boundary; every call returns a crv_status code and records
+ * a message for crv_last_error().
+ */
+#ifndef CRV_H
+#define CRV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct crv_plan_s* crv_plan_t;
+
+typedef enum crv_status {
+  CRV_OK = 0,
+  CRV_EINVAL = 1,        /* invalid argument (sizes, lambda, spin, batch, null pointer) */
+  CRV_ENOMEM = 2,        /* device allocation of tables or workspace failed */
+  CRV_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  CRV_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+  CRV_EUNSUPPORTED = 5   /* valid but not supported by this build (e.g. no GPU) */
+} crv_status;
+
+/* Azimuthal band-limit rule. The curvelet rule is the only one: N_j = L_j and the
+ * directional component is supported on |m| = l before rotation (Sec. II-B). */
+enum { CRV_NRULE_CURVELET = 0 };
+
+/* Plan flags. */
+enum {
+  CRV_F_REAL = 1,   /* spin-0 real signal: real maps and real W (conjugate symmetry, Sec. III-A-3) */
+  CRV_F_MIXED = 2,  /* split-FP32 contraction on tensor cores and FP32 FFTs; Delta recursion
+                       and the synthesis accumulation of f_lm stay FP64 */
+  CRV_F_W_FP32 = 4  /* store W_j as float instead of double */
+};
+
+/* Create a plan.
+ *   L         band limit, 2 <= L <= 4096
+ *   lambda    dilation parameter, lambda > 1 (Sec. II-B)
+ *   J0        lowest curvelet scale, J0 >= 0, J0 <= J; lambda^J0 >= |spin| so that
+ *             vartheta^j = arccos(-s/lambda^j) of Eq. (theta_peakj) exists
+ *   spin      s; CRV_F_REAL requires s = 0
+ *   nrule     CRV_NRULE_CURVELET
+ *   flags     CRV_F_* bits
+ *   max_batch largest B accepted by the transform calls (workspace is per map, so this
+ *             only bounds argument checks)
+ *   stream    CUDA stream used for the table build (Delta recursion)
+ * Builds the radial kernels kappa^(j) and scaling function (Sec. II-B), the rotated
+ * directional components zeta^(j) (Eq. after directionality_normalisation), the
+ * Delta^l = d^l(pi/2) tables (FP64, on the device), FFT tables and workspace.
+ * Synchronises the stream. On error *out is NULL. */
+int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule,
+                    unsigned flags, int max_batch, void* stream);
+
+/* Free a plan and all its device memory (synchronises the device first). NULL is ok. */
+int crv_plan_destroy(crv_plan_t plan);
+
+/* Sizes of a plan. Any output pointer may be NULL.
+ *   J                 largest scale
+ *   Lj[j], j=0..J     band limit of scale j (entries j < J0 are 0)
+ *   w_elems[j]        samples per map of W_j (L_j (2L_j-1)^2; 0 for j < J0)
+ *   L_phi             band limit of the scaling map
+ *   workspace_bytes   device memory the plan holds (tables + workspace)
+ * Lj and w_elems must have room for J+1 entries (J <= 64). */
+int crv_plan_info(crv_plan_t plan, int* J, int* Lj, size_t* w_elems, int* L_phi,
+                  size_t* workspace_bytes);
+
+/* Host copy of plan tables, for inspection and tests.
+ *   crv_plan_kernel:  psi[l][n + L_j - 1] = sPsi^(j)_ln (real, Eq. wav_factorized), l < L_j
+ *   crv_plan_scaling: phi[l] = sqrt(4pi/(2l+1)) Phi_l0 = sqrt(k_lambda(l/lambda^J0)), l < L
+ *   crv_plan_delta:   out[m'][n] = Delta^l_{m'n} for 0 <= m', n <= l (quarter table read
+ *                     back from the device; the other quadrants follow by symmetry) */
+int crv_plan_kernel(crv_plan_t plan, int j, double* psi_host);
+int crv_plan_scaling(crv_plan_t plan, double* phi_host);
+int crv_plan_delta(crv_plan_t plan, int l, double* out_host);
+
+/* Forward spin SHT: map [B][L][2L-1] -> f_lm [B][L*L] (complex double). Exact for
+ * band-limited maps (MW sampling theorem; same quadrature steps as Sec. III-A-2 with
+ * n = -s). */
+int crv_sht_fwd(crv_plan_t plan, const void* map, void* flm, int B, void* stream);
+
+/* Inverse spin SHT: f_lm [B][L*L] -> map [B][L][2L-1] (Eq. spin_sphericalHarmonics
+ * summed over l, m). With CRV_F_REAL the imaginary part is dropped. */
+int crv_sht_inv(crv_plan_t plan, const void* flm, void* map, int B, void* stream);
+
+/* Curvelet analysis from a map: forward SHT, then for each scale the inverse Wigner
+ * transform of (8pi^2/(2l+1)) f_lm Psi^(j)*_ln onto the SO(3) grid (Eqs.
+ * wav_harmonic_coeff, inverse_Fmnmp in general-n form, inverse_feul), and the scaling
+ * map (Eq. analysis_scaling_harmonic).
+ *   W     array of J+1 device pointers; W[j] for J0 <= j <= J receives [B][W_j] (see
+ *         conventions); entries j < J0 are ignored and may be NULL
+ *   Wphi  [B][L_phi][2L_phi-1]; may be NULL to skip the scaling map */
+int crv_analysis(crv_plan_t plan, const void* map, void* const* W, void* Wphi, int B, void* stream);
+
+/* Curvelet synthesis to a map: per scale the forward Wigner transform of W_j and the
+ * sum over n with Psi^(j)_ln, plus the scaling term (Eq. wav_synthesis_harmonic), then
+ * the inverse SHT. W[j] for J0 <= j <= J must be valid; Wphi may be NULL (treated as
+ * zero). */
+int crv_synthesis(crv_plan_t plan, const void* const* W, const void* Wphi, void* map, int B,
+                  void* stream);
+
+/* Harmonic-space forms: as crv_analysis / crv_synthesis but starting from / ending at
+ * f_lm [B][L*L] (no SHT). For CRV_F_REAL plans f_lm must satisfy
+ * f_{l,-m} = (-1)^m conj(f_lm); the synthesis output does. */
+int crv_analysis_lm(crv_plan_t plan, const void* flm, void* const* W, void* Wphi, int B, void* stream);
+int crv_synthesis_lm(crv_plan_t plan, const void* const* W, const void* Wphi, void* flm, int B,
+                     void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* crv_last_error(void);
+
+/* Human-readable name of a status code. */
+const char* crv_status_string(int status);
+
+/* Number of kernel launches this library has issued since load (all plans, all
+ * threads). Used to count device work inside timed regions. */
+unsigned long long crv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRV_H */

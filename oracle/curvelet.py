@@ -217,9 +217,11 @@ def band_limit(lam, j, L):
     return min(L, _ceil_pow(lam, j + 1))
 
 
-def L_phi(lam, J0):
-    """Band limit of the scaling map: ceil(lam^J0)."""
-    return max(1, _ceil_pow(lam, J0))
+def L_phi(lam, J0, L=None):
+    """Band limit of the scaling map: ceil(lam^J0), capped at the signal's band limit
+    L (Phi_l0 is only needed for l < L)."""
+    v = max(1, _ceil_pow(lam, J0))
+    return v if L is None else min(v, L)
 
 
 def kappa(lam, j, L):
@@ -293,7 +295,7 @@ def analysis_rings(flm, lam, j, s, L, rings=None, psi_j=None, method="risbo"):
 def scaling_map(flm, lam, J0, L):
     """Scaling coefficients W^Phi on the MW grid of band limit ceil(lam^J0): inverse
     spin-0 SHT of sqrt(4pi/(2l+1)) f_lm Phi*_l0 (Eq. swav_harmonic_coeff)."""
-    Lp = L_phi(lam, J0)
+    Lp = L_phi(lam, J0, L)
     ph = phi_scaling(lam, J0, Lp)
     c = np.zeros(Lp * Lp, dtype=np.complex128)
     for l in range(min(Lp, L)):
@@ -357,7 +359,7 @@ def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None):
         lib().orc_wigner_fwd_contract(Lj, _p(Y.view(np.float64)), _p(ps), _p(part.view(np.float64)), None)
         f[: Lj * Lj] += part
     if Wphi is not None:
-        Lp = L_phi(lam, J0)
+        Lp = L_phi(lam, J0, L)
         c = sht_forward(Wphi, Lp, 0)
         ph = phi_scaling(lam, J0, Lp)
         for l in range(min(Lp, L)):

@@ -1,0 +1,256 @@
+"""GB300-native spherical curvelet transform (arXiv:1511.05578): Python binding.
+
+Thin ctypes marshalling over libcrv.so, whose C ABI is include/crv.h. Every step of
+the transform runs in the library's CUDA kernels; this module only converts
+arguments (torch CUDA tensors or raw device pointers, streams) and raises on error
+codes. There is no CPU fallback: if libcrv.so is missing or no GPU is visible the
+calls raise.
+
+The functions carry the C names (crv_plan_create, crv_analysis, ...). `Plan` is a
+small convenience owner of a plan handle with tensor allocation helpers.
+"""
+import ctypes
+import os
+
+__all__ = [
+    "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
+    "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CrvError",
+    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_kernel",
+    "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
+    "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_last_error", "crv_status_string",
+    "crv_launch_count", "Plan",
+]
+
+CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED = range(6)
+CRV_NRULE_CURVELET = 0
+CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32 = 1, 2, 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+class CrvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib_path():
+    return os.path.join(_HERE, "libcrv.so")
+
+
+def load():
+    """Load libcrv.so (built by paper_1511_05578_gb300.build.build()); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = lib_path()
+    if not os.path.exists(p):
+        raise CrvError(CRV_EUNSUPPORTED, f"CUDA extension {p} is not built; run paper_1511_05578_gb300.build.build()")
+    h = ctypes.CDLL(p)
+    vp, i, u, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "crv_plan_create": (i, [ctypes.POINTER(vp), i, d, i, i, i, u, i, vp]),
+        "crv_plan_destroy": (i, [vp]),
+        "crv_plan_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i),
+                              ctypes.POINTER(sz)]),
+        "crv_plan_kernel": (i, [vp, i, ctypes.POINTER(d)]),
+        "crv_plan_scaling": (i, [vp, ctypes.POINTER(d)]),
+        "crv_plan_delta": (i, [vp, i, ctypes.POINTER(d)]),
+        "crv_sht_fwd": (i, [vp, vp, vp, i, vp]),
+        "crv_sht_inv": (i, [vp, vp, vp, i, vp]),
+        "crv_analysis": (i, [vp, vp, ctypes.POINTER(vp), vp, i, vp]),
+        "crv_synthesis": (i, [vp, ctypes.POINTER(vp), vp, vp, i, vp]),
+        "crv_analysis_lm": (i, [vp, vp, ctypes.POINTER(vp), vp, i, vp]),
+        "crv_synthesis_lm": (i, [vp, ctypes.POINTER(vp), vp, vp, i, vp]),
+        "crv_last_error": (ctypes.c_char_p, []),
+        "crv_status_string": (ctypes.c_char_p, [i]),
+        "crv_launch_count": (ctypes.c_ulonglong, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(h, name)
+        f.restype, f.argtypes = res, args
+    _lib = h
+    return h
+
+
+def _check(status):
+    if status != CRV_OK:
+        h = load()
+        raise CrvError(status, f"{h.crv_status_string(status).decode()}: {h.crv_last_error().decode()}")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("libcrv takes device memory: pass CUDA tensors")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer from {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _ptr_array(xs, n):
+    arr = (ctypes.c_void_p * n)()
+    for j, x in enumerate(xs):
+        arr[j] = _ptr(x)
+    return arr
+
+
+def crv_last_error():
+    return load().crv_last_error().decode()
+
+
+def crv_status_string(s):
+    return load().crv_status_string(int(s)).decode()
+
+
+def crv_launch_count():
+    return int(load().crv_launch_count())
+
+
+def crv_plan_create(L, lam, J0, spin=0, nrule=CRV_NRULE_CURVELET, flags=0, max_batch=1, stream=None):
+    h = load()
+    out = ctypes.c_void_p()
+    _check(h.crv_plan_create(ctypes.byref(out), int(L), float(lam), int(J0), int(spin), int(nrule), int(flags),
+                             int(max_batch), _stream(stream)))
+    return out
+
+
+def crv_plan_destroy(plan):
+    _check(load().crv_plan_destroy(plan))
+
+
+def crv_plan_info(plan):
+    h = load()
+    J = ctypes.c_int()
+    _check(h.crv_plan_info(plan, ctypes.byref(J), None, None, None, None))
+    n = J.value + 1
+    Lj = (ctypes.c_int * n)()
+    we = (ctypes.c_size_t * n)()
+    Lp = ctypes.c_int()
+    ws = ctypes.c_size_t()
+    _check(h.crv_plan_info(plan, ctypes.byref(J), Lj, we, ctypes.byref(Lp), ctypes.byref(ws)))
+    return {"J": J.value, "Lj": list(Lj), "w_elems": list(we), "L_phi": Lp.value, "workspace_bytes": ws.value}
+
+
+def crv_plan_kernel(plan, j, out):
+    """out: float64 numpy array of L_j * (2L_j - 1) entries (host)."""
+    _check(load().crv_plan_kernel(plan, int(j), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def crv_plan_scaling(plan, out):
+    _check(load().crv_plan_scaling(plan, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def crv_plan_delta(plan, l, out):
+    _check(load().crv_plan_delta(plan, int(l), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def crv_sht_fwd(plan, fmap, flm, B, stream=None):
+    _check(load().crv_sht_fwd(plan, _ptr(fmap), _ptr(flm), int(B), _stream(stream)))
+
+
+def crv_sht_inv(plan, flm, fmap, B, stream=None):
+    _check(load().crv_sht_inv(plan, _ptr(flm), _ptr(fmap), int(B), _stream(stream)))
+
+
+def crv_analysis(plan, fmap, W, Wphi, B, stream=None):
+    _check(load().crv_analysis(plan, _ptr(fmap), _ptr_array(W, len(W)), _ptr(Wphi), int(B), _stream(stream)))
+
+
+def crv_synthesis(plan, W, Wphi, fmap, B, stream=None):
+    _check(load().crv_synthesis(plan, _ptr_array(W, len(W)), _ptr(Wphi), _ptr(fmap), int(B), _stream(stream)))
+
+
+def crv_analysis_lm(plan, flm, W, Wphi, B, stream=None):
+    _check(load().crv_analysis_lm(plan, _ptr(flm), _ptr_array(W, len(W)), _ptr(Wphi), int(B), _stream(stream)))
+
+
+def crv_synthesis_lm(plan, W, Wphi, flm, B, stream=None):
+    _check(load().crv_synthesis_lm(plan, _ptr_array(W, len(W)), _ptr(Wphi), _ptr(flm), int(B), _stream(stream)))
+
+
+class Plan:
+    """Owns a plan handle; allocates correctly shaped torch tensors for its data."""
+
+    def __init__(self, L, lam=2.0, J0=2, spin=0, flags=0, max_batch=1, stream=None):
+        self.L, self.lam, self.J0, self.spin, self.flags, self.max_batch = L, lam, J0, spin, flags, max_batch
+        self.handle = crv_plan_create(L, lam, J0, spin, CRV_NRULE_CURVELET, flags, max_batch, stream)
+        info = crv_plan_info(self.handle)
+        self.J, self.Lj, self.L_phi, self.bytes = info["J"], info["Lj"], info["L_phi"], info["workspace_bytes"]
+        self.real = bool(flags & CRV_F_REAL)
+        self.w_dtype_name = "float32" if flags & CRV_F_W_FP32 else "float64"
+
+    def close(self):
+        if self.handle is not None:
+            crv_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- allocation helpers (torch) --
+    def _t(self):
+        import torch
+        return torch
+
+    def map_tensor(self, B=1, L=None):
+        torch = self._t()
+        L = self.L if L is None else L
+        shape = (B, L, 2 * L - 1) + (() if self.real else (2,))
+        return torch.zeros(shape, dtype=torch.float64, device="cuda")
+
+    def flm_tensor(self, B=1):
+        torch = self._t()
+        return torch.zeros((B, self.L * self.L), dtype=torch.complex128, device="cuda")
+
+    def W_tensors(self, B=1):
+        torch = self._t()
+        dt = torch.float32 if self.w_dtype_name == "float32" else torch.float64
+        out = []
+        for j in range(self.J + 1):
+            if j < self.J0:
+                out.append(None)
+                continue
+            Lb = self.Lj[j]
+            N = 2 * Lb - 1
+            shape = (B, Lb, N, N) + (() if self.real else (2,))
+            out.append(torch.zeros(shape, dtype=dt, device="cuda"))
+        return out
+
+    def Wphi_tensor(self, B=1):
+        return self.map_tensor(B, self.L_phi)
+
+    def kernel(self, j):
+        import numpy as np
+        Lb = self.Lj[j]
+        out = np.zeros(Lb * (2 * Lb - 1))
+        return crv_plan_kernel(self.handle, j, out).reshape(Lb, 2 * Lb - 1)
+
+    def scaling(self):
+        import numpy as np
+        return crv_plan_scaling(self.handle, np.zeros(self.L))
+
+    def delta(self, l):
+        import numpy as np
+        return crv_plan_delta(self.handle, l, np.zeros((l + 1) * (l + 1))).reshape(l + 1, l + 1)

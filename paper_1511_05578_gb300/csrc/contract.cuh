@@ -1,0 +1,282 @@
+// Delta contractions of the Wigner transforms and the spin SHT (CUDA-core form).
+//
+// Analysis (inverse Wigner, Eq. inverse_Fmnmp in general-n form with the
+// coefficients of Eq. wav_harmonic_coeff folded in):
+//   X_{m n m'} = i^{n-m} sum_l Delta^l_{m'm} Delta^l_{m'n} f_lm Psi_ln,   m' >= 0.
+// Per m' this is a product U(m') V(m') with U_{m,l} = Delta^l_{m'm} f_lm and
+// V_{l,n} = Delta^l_{m'n} Psi_ln, both built on the fly from the quarter Delta table.
+//
+// Synthesis (forward Wigner, Eq. flml in general-n form, then the n-sum of Eq.
+// wav_synthesis_harmonic):
+//   f_lm += sum_{m'>=0} Delta^l_{m'm} sum_n (Delta^l_{m'n} Psi_ln) Y'_{m n m'},
+// where Y' already carries i^{m-n}. Per m' the inner sum is a product Y'(m') V(m')^T;
+// the outer sum over m' accumulates in FP64 registers and is flushed with FP64
+// atomics once per block.
+#pragma once
+#include "transforms.cuh"
+
+namespace crv {
+
+// Delta^l_{a,b} for a >= 0 and any b, from the quarter table Q[a][l][|b|].
+template <class T>
+__device__ __forceinline__ T delta_q(const T* __restrict__ Q, int Lmax, int a, int l, int b) {
+  const int ab = b < 0 ? -b : b;
+  T v = Q[((size_t)a * Lmax + l) * Lmax + ab];
+  if (b < 0 && ((l + a) & 1)) v = -v;
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Analysis contraction. Block tile 32 (m) x 64 (n), K-step 16, 256 threads,
+// each thread 2 x 4 outputs. grid = (ceil(Nc/64), ceil(Mc/32), Lb).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) contract_analysis_kernel(const T* __restrict__ Q, int Lmax,
+                                                                const cx<double>* __restrict__ flm,
+                                                                const T* __restrict__ psi, int Lb, ColSet cs,
+                                                                cx<T>* __restrict__ X) {
+  constexpr int TM = 32, TN = 64, TK = 16;
+  __shared__ cx<T> As[TK][TM];
+  __shared__ T Bs[TK][TN];
+  const int N = 2 * Lb - 1;
+  const int mp = blockIdx.z;
+  const int mi0 = blockIdx.y * TM, ni0 = blockIdx.x * TN;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  // smallest |m|, |n| in the tile -> first useful l
+  int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + TM, cs.Mc) - 1;
+  int nlo = cs.n0 + cs.nstep * ni0, nhi = cs.n0 + cs.nstep * (min(ni0 + TN, cs.Nc) - 1);
+  int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
+  int bmin = (nlo <= 0 && nhi >= 0) ? 0 : min(abs(nlo), abs(nhi));
+  int lstart = max(mp, max(amin, bmin));
+  cx<T> acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(0, 0);
+  for (int l0 = lstart; l0 < Lb; l0 += TK) {
+    // A tile: 512 complex entries, 2 per thread
+    for (int t = threadIdx.x; t < TK * TM; t += 256) {
+      const int k = t / TM, i = t % TM, l = l0 + k, mi = mi0 + i;
+      cx<T> v = mk<T>(0, 0);
+      if (l < Lb && mi < cs.Mc) {
+        const int m = cs.m0 + mi;
+        if (abs(m) <= l) {
+          const cx<double> f = flm[l * l + l + m];
+          const T d = delta_q(Q, Lmax, mp, l, m);
+          v = mk<T>(d * (T)f.re, d * (T)f.im);
+        }
+      }
+      As[k][i] = v;
+    }
+    for (int t = threadIdx.x; t < TK * TN; t += 256) {
+      const int k = t / TN, j = t % TN, l = l0 + k, ni = ni0 + j;
+      T v = 0;
+      if (l < Lb && ni < cs.Nc) {
+        const int n = cs.n0 + cs.nstep * ni;
+        if (abs(n) <= l) v = delta_q(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)];
+      }
+      Bs[k][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      const cx<T> a0 = As[k][ty * 2], a1 = As[k][ty * 2 + 1];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const T b = Bs[k][tx * 4 + j];
+        acc[0][j].re += a0.re * b; acc[0][j].im += a0.im * b;
+        acc[1][j].re += a1.re * b; acc[1][j].im += a1.im * b;
+      }
+    }
+    __syncthreads();
+  }
+  const size_t plane = (size_t)cs.Mc * cs.Nc;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int mi = mi0 + ty * 2 + i;
+    if (mi >= cs.Mc) continue;
+    const int m = cs.m0 + mi;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ni = ni0 + tx * 4 + j;
+      if (ni >= cs.Nc) continue;
+      const int n = cs.n0 + cs.nstep * ni;
+      X[(size_t)mp * plane + (size_t)mi * cs.Nc + ni] = mul_ipow(acc[i][j], imod(n - m, 4));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Synthesis contraction. Block tile 32 (m) x 32 (l), 256 threads, 2 x 2 outputs
+// per thread, K-step 16 over n, a chunk of m' values per block.
+// grid = (ceil(Lb/32), ceil(Mc/32), ceil(Lb/mchunk)).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) contract_synthesis_kernel(const T* __restrict__ Q, int Lmax,
+                                                                 const cx<T>* __restrict__ Y,
+                                                                 const T* __restrict__ psi, int Lb, ColSet cs,
+                                                                 int mchunk, cx<double>* __restrict__ flm) {
+  constexpr int TM = 32, TL = 32, TK = 16;
+  __shared__ cx<T> Ys[TM][TK + 1];
+  __shared__ T Vs[TK][TL];
+  const int N = 2 * Lb - 1;
+  const int l0 = blockIdx.x * TL, mi0 = blockIdx.y * TM;
+  const int lhi = min(l0 + TL, Lb) - 1;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + TM, cs.Mc) - 1;
+  const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
+  if (amin > lhi) return;
+  // n range with |n| <= lhi
+  int ni_lo = 0, ni_hi = cs.Nc;  // [ni_lo, ni_hi)
+  {
+    int nmin = -lhi;
+    int d = nmin - cs.n0;
+    ni_lo = d <= 0 ? 0 : (d + cs.nstep - 1) / cs.nstep;
+    int dmax = lhi - cs.n0;
+    ni_hi = dmax < 0 ? 0 : min(cs.Nc, dmax / cs.nstep + 1);
+  }
+  cx<double> facc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) { facc[i][0] = mk(0.0, 0.0); facc[i][1] = mk(0.0, 0.0); }
+  const size_t plane = (size_t)cs.Mc * cs.Nc;
+  const int mp_end = min((int)(blockIdx.z + 1) * mchunk, lhi + 1);
+  for (int mp = blockIdx.z * mchunk; mp < mp_end; ++mp) {
+    cx<T> z[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) { z[i][0] = mk<T>(0, 0); z[i][1] = mk<T>(0, 0); }
+    for (int nk = ni_lo; nk < ni_hi; nk += TK) {
+      for (int t = threadIdx.x; t < TM * TK; t += 256) {
+        const int i = t / TK, k = t % TK, mi = mi0 + i, ni = nk + k;
+        Ys[i][k] = (mi < cs.Mc && ni < ni_hi) ? Y[(size_t)mp * plane + (size_t)mi * cs.Nc + ni] : mk<T>(0, 0);
+      }
+      for (int t = threadIdx.x; t < TK * TL; t += 256) {
+        const int k = t / TL, j = t % TL, ni = nk + k, l = l0 + j;
+        T v = 0;
+        if (ni < ni_hi && l < Lb && l >= mp) {
+          const int n = cs.n0 + cs.nstep * ni;
+          if (abs(n) <= l) v = delta_q(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)];
+        }
+        Vs[k][j] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < TK; ++k) {
+        const cx<T> y0 = Ys[ty * 2][k], y1 = Ys[ty * 2 + 1][k];
+        const T v0 = Vs[k][tx * 2], v1 = Vs[k][tx * 2 + 1];
+        z[0][0].re += y0.re * v0; z[0][0].im += y0.im * v0;
+        z[0][1].re += y0.re * v1; z[0][1].im += y0.im * v1;
+        z[1][0].re += y1.re * v0; z[1][0].im += y1.im * v0;
+        z[1][1].re += y1.re * v1; z[1][1].im += y1.im * v1;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int mi = mi0 + ty * 2 + i;
+      if (mi >= cs.Mc) continue;
+      const int m = cs.m0 + mi;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int l = l0 + tx * 2 + j;
+        if (l >= Lb || l < mp || abs(m) > l) continue;
+        const double d = (double)delta_q(Q, Lmax, mp, l, m);
+        facc[i][j].re += d * (double)z[i][j].re;
+        facc[i][j].im += d * (double)z[i][j].im;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int mi = mi0 + ty * 2 + i;
+    if (mi >= cs.Mc) continue;
+    const int m = cs.m0 + mi;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int l = l0 + tx * 2 + j;
+      if (l >= Lb || abs(m) > l) continue;
+      atomicAdd(&flm[l * l + l + m].re, facc[i][j].re);
+      atomicAdd(&flm[l * l + l + m].im, facc[i][j].im);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SHT contractions (FP64; O(L^3) total).
+// Forward:  f_lm = sqrt((2l+1)/4pi) sum_{m'>=0} Delta^l_{m'm} Delta^l_{m',-s} G'[m'][mi]
+//           (G' carries (-1)^s i^{m+s} and the folding over +-m').
+// Inverse:  G[m'][mi] = (-1)^s i^{-(m+s)} sum_l sqrt((2l+1)/4pi) Delta^l_{m'm} Delta^l_{m',-s} f_lm.
+// ---------------------------------------------------------------------------
+static __global__ void sht_fwd_contract_kernel(const double* __restrict__ Q, int Lmax, const cx<double>* __restrict__ G,
+                                        int Ls, int s, int Mc, int m0, cx<double>* __restrict__ flm) {
+  const int mi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y;
+  if (mi >= Mc) return;
+  const int m = m0 + mi;
+  if (abs(m) > l) return;
+  cx<double> acc = mk(0.0, 0.0);
+  if (l >= abs(s)) {
+    for (int mp = 0; mp <= l; ++mp) {
+      const double d = delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, -s);
+      const cx<double> g = G[(size_t)mp * Mc + mi];
+      acc.re += d * g.re; acc.im += d * g.im;
+    }
+  }
+  const double nrm = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+  flm[l * l + l + m] = acc * nrm;
+}
+
+static __global__ void sht_inv_contract_kernel(const double* __restrict__ Q, int Lmax, const cx<double>* __restrict__ flm,
+                                        int Ls, int s, int Mc, int m0, cx<double>* __restrict__ G) {
+  const int mi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mp = blockIdx.y;
+  if (mi >= Mc) return;
+  const int m = m0 + mi;
+  cx<double> acc = mk(0.0, 0.0);
+  int lstart = max(mp, max(abs(m), abs(s)));
+  for (int l = lstart; l < Ls; ++l) {
+    const double d = sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, -s);
+    const cx<double> f = flm[l * l + l + m];
+    acc.re += d * f.re; acc.im += d * f.im;
+  }
+  acc = mul_ipow(acc, imod(-(m + s) + 2 * s, 4));
+  G[(size_t)mp * Mc + mi] = acc;
+}
+
+// f_{l,-m} = (-1)^m conj(f_lm) for m > 0 (real signals); zero for l < |s| or l >= Lkeep.
+static __global__ void flm_finish_kernel(cx<double>* __restrict__ flm, int L, int s, bool real) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L * L) return;
+  const int l = (int)sqrt((double)i);
+  int ll = l;
+  if (ll * ll > i) --ll;
+  if ((ll + 1) * (ll + 1) <= i) ++ll;
+  const int m = i - ll * ll - ll;
+  if (ll < abs(s)) { flm[i] = mk(0.0, 0.0); return; }
+  if (real && m < 0) {
+    cx<double> v = flm[ll * ll + ll - m];
+    v = conj(v);
+    if ((-m) & 1) v = mk(-v.re, -v.im);
+    flm[i] = v;
+  }
+}
+
+// c_lm = phi_l f_lm (l < Lp), packed for band limit Lp; or f_lm += phi_l c_lm.
+static __global__ void scaling_apply_kernel(const double* __restrict__ phi, int Lp, const cx<double>* __restrict__ in,
+                                     cx<double>* __restrict__ out, bool accumulate) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Lp * Lp) return;
+  int l = (int)sqrt((double)i);
+  if (l * l > i) --l;
+  if ((l + 1) * (l + 1) <= i) ++l;
+  const cx<double> v = in[i] * phi[l];
+  if (accumulate) out[i] = out[i] + v;
+  else out[i] = v;
+}
+
+template <class T>
+__global__ void cast_flm_kernel(const cx<double>* __restrict__ in, cx<T>* __restrict__ out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = mk<T>((T)in[i].re, (T)in[i].im);
+}
+
+}  // namespace crv

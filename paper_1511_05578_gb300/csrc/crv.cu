@@ -1,0 +1,793 @@
+// libcrv host side: plan construction, per-scale pipelines and the C ABI of
+// include/crv.h. Device work lives in delta.cu, transforms.cuh, contract.cuh and
+// tc_contract.cu.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <atomic>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/crv.h"
+#include "contract.cuh"
+
+namespace crv {
+
+static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool launch_ok(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+  }
+  return true;
+}
+static int fail(int code, const std::string& msg) { g_err = msg; return code; }
+
+cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_e, cudaStream_t st);
+// tensor-core contractions (tc_contract.cu)
+bool tc_analysis(const float* Q32, int Lmax, const cx<double>* flm, const float* psi, int Lb, ColSet cs,
+                 cx<float>* X, void* scratch, size_t scratch_bytes, cudaStream_t st);
+bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, const float* psi, int Lb, ColSet cs,
+                  cx<double>* flm, void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t tc_scratch_bytes(int Lmax, int Mc, int Nc);
+
+// ---------------------------------------------------------------------------
+// Host numerics for the plan tables
+// ---------------------------------------------------------------------------
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1, p2 = 0;
+      for (int k = 1; k <= n; ++k) { double p3 = p2; p2 = p1; p1 = ((2.0 * k - 1) * z * p2 - (k - 1.0) * p3) / k; }
+      pp = n * (z * p1 - p2) / (z * z - 1);
+      double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p1 = 1, p2 = 0;
+    for (int k = 1; k <= n; ++k) { double p3 = p2; p2 = p1; p1 = ((2.0 * k - 1) * z * p2 - (k - 1.0) * p3) / k; }
+    pp = n * (z * p1 - p2) / (z * z - 1);
+    x[i] = z;
+    w[i] = 2.0 / ((1 - z * z) * pp * pp);
+  }
+}
+
+// k_lambda(t) of Sec. II-B: int_t^1 s_lambda(x)^2 / x dx normalised by the integral
+// from 1/lambda; composite Gauss-Legendre (64 panels x 20 points).
+struct KLambda {
+  double lam, norm;
+  std::vector<double> gx, gw;
+  static double sfun(double t) { return (t > -1 && t < 1) ? std::exp(-1.0 / (1.0 - t * t)) : 0.0; }
+  double integrand(double x) const {
+    double v = sfun(2 * lam / (lam - 1) * (x - 1 / lam) - 1);
+    return v * v / x;
+  }
+  double integral(double a, double b) const {
+    if (b <= a) return 0;
+    const int panels = 64;
+    double h = (b - a) / panels, acc = 0;
+    for (int p = 0; p < panels; ++p) {
+      double c = a + (p + 0.5) * h;
+      for (size_t i = 0; i < gx.size(); ++i) acc += gw[i] * integrand(c + 0.5 * h * gx[i]);
+    }
+    return acc * 0.5 * h;
+  }
+  explicit KLambda(double l) : lam(l) { gauss_legendre(20, gx, gw); norm = integral(1 / lam, 1); }
+  double operator()(double t) const {
+    if (t < 1 / lam) return 1.0;
+    if (t >= 1) return 0.0;
+    return integral(t, 1) / norm;
+  }
+};
+
+static int ceil_pow(double lam, int e) {
+  double v = std::pow(lam, e), r = std::round(v);
+  if (std::fabs(v - r) < 1e-9 * std::max(1.0, v)) return (int)r;
+  return (int)std::ceil(v);
+}
+
+// d^l_{k,l}(theta) for k = -l..l: sqrt(C(2l,l+k)) sin(t/2)^{l-k} cos(t/2)^{l+k}
+// (Eq. wigner_sum_reln, one surviving term), by ratios from the largest entry and
+// normalised with sum_k d^2 = 1 (a column of an orthogonal matrix).
+static void edge_row(int l, double sh, double ch, std::vector<double>& out) {
+  out.assign(2 * l + 1, 0.0);
+  if (l == 0) { out[0] = 1.0; return; }
+  if (sh == 0.0) { out[2 * l] = 1.0; return; }
+  if (ch == 0.0) { out[0] = 1.0; return; }
+  const double rat = ch / sh;
+  // ratio r_k = d_{k+1}/d_k = sqrt((l-k)/(l+k+1)) * ch/sh; peak where r_k crosses 1
+  int kp = -l;
+  while (kp < l && std::sqrt((double)(l - kp) / (l + kp + 1)) * rat > 1.0) ++kp;
+  out[kp + l] = 1.0;
+  for (int k = kp; k < l; ++k) {
+    double v = out[k + l] * std::sqrt((double)(l - k) / (l + k + 1)) * rat;
+    out[k + 1 + l] = v;
+    if (v < 1e-300) break;
+  }
+  for (int k = kp; k > -l; --k) {
+    double v = out[k + l] / (std::sqrt((double)(l - k + 1) / (l + k)) * rat);
+    out[k - 1 + l] = v;
+    if (v < 1e-300) break;
+  }
+  double s2 = 0;
+  for (double v : out) s2 += v * v;
+  const double nrm = 1.0 / std::sqrt(s2);
+  for (double& v : out) v *= nrm;
+}
+
+static void host_fft(std::vector<std::complex<double>>& a, int sign) {
+  const int n = (int)a.size();
+  for (int i = 1, j = 0; i < n; ++i) {
+    int bit = n >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (int len = 2; len <= n; len <<= 1) {
+    for (int i = 0; i < n; i += len)
+      for (int k = 0; k < len / 2; ++k) {
+        double ang = sign * 2 * M_PI * k / len;
+        std::complex<double> w(std::cos(ang), std::sin(ang));
+        std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+        a[i + k] = u + v;
+        a[i + k + len / 2] = u - v;
+      }
+  }
+}
+
+static int next_pow2(int n) { int p = 1; while (p < n) p <<= 1; return p; }
+
+}  // namespace crv
+
+using namespace crv;
+
+// ---------------------------------------------------------------------------
+// The plan
+// ---------------------------------------------------------------------------
+struct FftSet {
+  DftTab<double> d; DftTab<float> f;
+  CorrTab<double> cd; CorrTab<float> cf;
+};
+
+struct crv_plan_s {
+  int L = 0, J0 = 0, J = 0, spin = 0, max_batch = 0, Lphi = 1;
+  unsigned flags = 0;
+  double lambda = 2;
+  bool real = false, mixed = false, wfp32 = false;
+  std::vector<int> Lj;
+  std::vector<double> kappa;  // [J+1][L]
+  std::vector<double> phi;    // [L]
+  std::vector<std::vector<double>> psi;  // per j: [Lj][2Lj-1]
+  double* dQ = nullptr;
+  float* dQ32 = nullptr;
+  std::vector<double*> dpsi;
+  std::vector<float*> dpsi32;
+  double* dphi = nullptr;
+  std::map<int, FftSet> fft;  // keyed by band limit Lb
+  // workspace
+  cx<double>* wflm = nullptr;
+  cx<double>* wflm2 = nullptr;
+  cx<double>* wF = nullptr;
+  cx<double>* wG = nullptr;
+  void* wX = nullptr;
+  void* wXb = nullptr;
+  void* wR = nullptr;
+  void* wTC = nullptr;
+  size_t tc_bytes = 0;
+  size_t vol_bytes = 0, ring_bytes = 0;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+
+  template <class P> P* dalloc(size_t n, int* status) {
+    if (*status != CRV_OK) return nullptr;
+    void* p = nullptr;
+    size_t b = n * sizeof(P);
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *status = fail(CRV_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+      return nullptr;
+    }
+    allocs.push_back(p);
+    bytes += b;
+    return (P*)p;
+  }
+  ~crv_plan_s() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  int mc(int Lb) const { return real ? Lb : 2 * Lb - 1; }
+  int m0(int Lb) const { return real ? 0 : -(Lb - 1); }
+  int nstep() const { return spin == 0 ? 2 : 1; }
+  int n0(int Lb) const {
+    if (spin != 0) return -(Lb - 1);
+    int n = -(Lb - 1);
+    if (n & 1) n += 1;
+    return n;
+  }
+  int nc(int Lb) const { return (-n0(Lb) - n0(Lb)) / nstep() + 1; }
+  ColSet colset(int Lb) const { ColSet c; c.Mc = mc(Lb); c.m0 = m0(Lb); c.Nc = nc(Lb); c.n0 = n0(Lb); c.nstep = nstep(); c.extra = 0; return c; }
+};
+
+template <class T> static const DftTab<T>& dft_of(const FftSet& s);
+template <> const DftTab<double>& dft_of<double>(const FftSet& s) { return s.d; }
+template <> const DftTab<float>& dft_of<float>(const FftSet& s) { return s.f; }
+template <class T> static const CorrTab<T>& corr_of(const FftSet& s);
+template <> const CorrTab<double>& corr_of<double>(const FftSet& s) { return s.cd; }
+template <> const CorrTab<float>& corr_of<float>(const FftSet& s) { return s.cf; }
+
+static int build_fft(crv_plan_s* p, int Lb) {
+  if (p->fft.count(Lb)) return CRV_OK;
+  const int N = 2 * Lb - 1;
+  const int P = next_pow2(2 * N - 1);
+  const int Q = next_pow2(4 * Lb - 3 > 1 ? 4 * Lb - 3 : 1);
+  std::vector<std::complex<double>> tw(P), chirp(N), kf(P, 0.0), ki(P, 0.0), twq(Q), wv(Q, 0.0);
+  for (int k = 0; k < P; ++k) tw[k] = std::polar(1.0, -2 * M_PI * (double)k / P);
+  for (int t = 0; t < N; ++t) {
+    long long r = ((long long)t * t) % (2LL * N);
+    chirp[t] = std::polar(1.0, -M_PI * (double)r / N);
+  }
+  for (int t = -(N - 1); t <= N - 1; ++t) {
+    const int a = t < 0 ? -t : t;
+    kf[((t % P) + P) % P] = std::conj(chirp[a]);  // forward: b_t = conj(h_t)
+    ki[((t % P) + P) % P] = chirp[a];             // inverse: b_t = conj(conj(h_t))
+  }
+  host_fft(kf, -1);
+  host_fft(ki, -1);
+  for (auto& v : kf) v /= (double)P;
+  for (auto& v : ki) v /= (double)P;
+  for (int k = 0; k < Q; ++k) twq[k] = std::polar(1.0, -2 * M_PI * (double)k / Q);
+  // v[t] = w(-t), t in [-(2Lb-2), 2Lb-2]; w(p) = int_0^pi sin(b) e^{i p b} db
+  for (int t = -(2 * Lb - 2); t <= 2 * Lb - 2; ++t) {
+    const int pp = -t;
+    std::complex<double> w;
+    if (pp % 2 == 0) w = 2.0 / (1.0 - (double)pp * pp);
+    else if (pp == 1) w = std::complex<double>(0, M_PI / 2);
+    else if (pp == -1) w = std::complex<double>(0, -M_PI / 2);
+    else w = 0.0;
+    wv[((t % Q) + Q) % Q] = w;
+  }
+  host_fft(wv, -1);
+  for (auto& v : wv) v /= (double)Q;
+
+  int st = CRV_OK;
+  FftSet s;
+  auto up = [&](const std::vector<std::complex<double>>& v, cx<double>*& dd, cx<float>*& df) {
+    dd = p->dalloc<cx<double>>(v.size(), &st);
+    df = p->dalloc<cx<float>>(v.size(), &st);
+    if (st != CRV_OK) return;
+    std::vector<cx<double>> hd(v.size());
+    std::vector<cx<float>> hf(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      hd[i] = mk(v[i].real(), v[i].imag());
+      hf[i] = mk((float)v[i].real(), (float)v[i].imag());
+    }
+    cudaMemcpy(dd, hd.data(), v.size() * sizeof(cx<double>), cudaMemcpyHostToDevice);
+    cudaMemcpy(df, hf.data(), v.size() * sizeof(cx<float>), cudaMemcpyHostToDevice);
+  };
+  cx<double>* d; cx<float>* f;
+  s.d.N = s.f.N = N; s.d.P = s.f.P = P;
+  up(tw, d, f); s.d.tw = d; s.f.tw = f;
+  up(chirp, d, f); s.d.chirp = d; s.f.chirp = f;
+  up(kf, d, f); s.d.khat_f = d; s.f.khat_f = f;
+  up(ki, d, f); s.d.khat_i = d; s.f.khat_i = f;
+  s.cd.Q = s.cf.Q = Q;
+  up(twq, d, f); s.cd.tw = d; s.cf.tw = f;
+  up(wv, d, f); s.cd.what = d; s.cf.what = f;
+  if (st != CRV_OK) return st;
+  p->fft[Lb] = s;
+  return CRV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch helpers
+// ---------------------------------------------------------------------------
+static const size_t kSmemBudget = 200 * 1024;
+
+template <class K>
+static bool set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  static std::map<const void*, size_t> done;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  auto it = done.find((const void*)kernel);
+  if (it != done.end() && it->second >= bytes) return true;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    g_err = "cudaFuncSetAttribute(max dynamic smem) failed";
+    return false;
+  }
+  done[(const void*)kernel] = bytes;
+  return true;
+}
+
+template <class T, bool COLFAST, class Ld, class St>
+static bool run_cols(const DftTab<T>& tb, int sign, int ncols, Ld ld, St st, cudaStream_t s) {
+  if (ncols <= 0) return true;
+  const size_t per = 2 * (size_t)tb.P * sizeof(cx<T>);
+  int nb = (int)std::max<size_t>(1, std::min<size_t>(32, kSmemBudget / per));
+  const int maxnb = std::max(1, ncols / (2 * 152));
+  nb = std::min(nb, maxnb);
+  const size_t smem = per * nb;
+  auto kern = dft_cols_kernel<T, COLFAST, Ld, St>;
+  if (!set_smem(kern, smem)) return false;
+  int grid = (ncols + nb - 1) / nb;
+  grid = std::min(grid, 152 * 16);
+  kern<<<grid, 256, smem, s>>>(tb, sign, ncols, nb, ld, st);
+  count_launch();
+  return launch_ok("dft_cols_kernel");
+}
+
+template <class T>
+static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y, ColSet cs, T scale,
+                          int pa, int pb, int pc, cudaStream_t s) {
+  const DftTab<T>& tb = dft_of<T>(fs);
+  const CorrTab<T>& ct = corr_of<T>(fs);
+  const int S = std::max(tb.P, ct.Q);
+  const size_t per = 2 * (size_t)S * sizeof(cx<T>);
+  int nb = (int)std::max<size_t>(1, std::min<size_t>(32, kSmemBudget / per));
+  nb = std::min(nb, std::max(1, ncols / (2 * 152)));
+  const size_t smem = per * nb;
+  if (!set_smem(beta_quad_kernel<T>, smem)) return false;
+  int grid = std::min((ncols + nb - 1) / nb, 152 * 16);
+  beta_quad_kernel<T><<<grid, 256, smem, s>>>(tb, ct, ncols, nb, Lb, Xb, Y, cs, scale, pa, pb, pc);
+  count_launch();
+  return launch_ok("beta_quad_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Spin SHT on the MW grid (always FP64)
+// ---------------------------------------------------------------------------
+static bool sht_forward(crv_plan_s* p, const double* map, cx<double>* flm, int Ls, int s, bool real, cudaStream_t st) {
+  const FftSet& fs = p->fft.at(Ls);
+  const int N = 2 * Ls - 1;
+  const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
+  LdMapRowT<double> ld{LdMapRow{map, N, real}};
+  StSHTRow<double> sr{p->wF, Mc, m0, N, 1.0 / N};
+  if (!run_cols<double, false>(fs.d, -1, Ls, ld, sr, st)) return false;
+  ColSet cs{Mc, m0, 1, 0, 1, s};
+  if (!run_beta_quad<double>(fs, Ls, Mc, p->wF, p->wG, cs, 2 * M_PI, 1, 0, imod(3 * s, 4), st)) return false;
+  cudaMemsetAsync(flm, 0, sizeof(cx<double>) * Ls * Ls, st);
+  dim3 g((Mc + 127) / 128, Ls);
+  sht_fwd_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, p->wG, Ls, s, Mc, m0, flm);
+  count_launch();
+  if (!launch_ok("sht_fwd_contract_kernel")) return false;
+  flm_finish_kernel<<<(Ls * Ls + 255) / 256, 256, 0, st>>>(flm, Ls, s, real);
+  count_launch();
+  return launch_ok("flm_finish_kernel");
+}
+
+static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int Ls, int s, bool real, cudaStream_t st) {
+  const FftSet& fs = p->fft.at(Ls);
+  const int N = 2 * Ls - 1;
+  const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
+  dim3 g((Mc + 127) / 128, Ls);
+  sht_inv_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, flm, Ls, s, Mc, m0, p->wG);
+  count_launch();
+  if (!launch_ok("sht_inv_contract_kernel")) return false;
+  ColSet cs{Mc, m0, 1, 0, 1, s};
+  LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs};
+  StRows<double> sr{p->wF, Mc, Ls};
+  if (!run_cols<double, true>(fs.d, +1, Mc, lb, sr, st)) return false;
+  LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
+  StMapRow sm{map, N, real};
+  return run_cols<double, false>(fs.d, +1, Ls, lr, sm, st);
+}
+
+// ---------------------------------------------------------------------------
+// Wigner transforms of one scale
+// ---------------------------------------------------------------------------
+template <class T> static const T* q_of(crv_plan_s* p);
+template <> const double* q_of<double>(crv_plan_s* p) { return p->dQ; }
+template <> const float* q_of<float>(crv_plan_s* p) { return p->dQ32; }
+template <class T> static const T* psi_of(crv_plan_s* p, int j);
+template <> const double* psi_of<double>(crv_plan_s* p, int j) { return p->dpsi[j]; }
+template <> const float* psi_of<float>(crv_plan_s* p, int j) { return p->dpsi32[j]; }
+
+static int ring_chunk(crv_plan_s* p, int Lb, size_t elem) {
+  const int N = 2 * Lb - 1;
+  const size_t per = (size_t)N * std::max(p->mc(Lb), p->nc(Lb)) * elem;
+  return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lb, p->ring_bytes / per));
+}
+
+template <class T, class OutT>
+static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, OutT* W, cudaStream_t st) {
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  const FftSet& fs = p->fft.at(Lb);
+  ColSet cs = p->colset(Lb);
+  cx<T>* X = (cx<T>*)p->wX;
+  cx<T>* Xb = (cx<T>*)p->wXb;
+  cx<T>* R = (cx<T>*)p->wR;
+  bool used_tc = false;
+  if constexpr (sizeof(T) == 4) {
+    if (p->wTC) {
+      if (!tc_analysis(p->dQ32, p->L, flm, p->dpsi32[j], Lb, cs, (cx<float>*)X, p->wTC, p->tc_bytes, st)) return false;
+      used_tc = true;
+    }
+  }
+  if (!used_tc) {
+    dim3 g((cs.Nc + 63) / 64, (cs.Mc + 31) / 32, Lb);
+    contract_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, X);
+    count_launch();
+    if (!launch_ok("contract_analysis_kernel")) return false;
+  }
+  const int ncols = cs.Mc * cs.Nc;
+  if (!run_cols<T, true>(dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs}, StRows<T>{Xb, ncols, Lb}, st))
+    return false;
+  const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
+  const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
+  for (int b0 = 0; b0 < Lb; b0 += Rr) {
+    const int nr = std::min(Rr, Lb - b0);
+    LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
+    StContig<T> sc{R, N};
+    if (!run_cols<T, false>(dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
+    LdRingM<T> lm{R, cs.Mc, cs.m0, N, p->real};
+    StW<T, OutT> sw{W + (size_t)b0 * wstride, N, p->real};
+    if (!run_cols<T, true>(dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
+  }
+  return true;
+}
+
+template <class T, class InT>
+static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double>* flm, cudaStream_t st) {
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  const FftSet& fs = p->fft.at(Lb);
+  ColSet cs = p->colset(Lb);
+  cx<T>* Y = (cx<T>*)p->wX;
+  cx<T>* Xb = (cx<T>*)p->wXb;
+  cx<T>* R = (cx<T>*)p->wR;
+  const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
+  const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
+  for (int b0 = 0; b0 < Lb; b0 += Rr) {
+    const int nr = std::min(Rr, Lb - b0);
+    LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, p->real};
+    StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
+    if (!run_cols<T, false>(dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
+    LdRingA<T> la{R, cs.Nc, N};
+    StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N};
+    if (!run_cols<T, true>(dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
+  }
+  const int ncols = cs.Mc * cs.Nc;
+  if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
+  if constexpr (sizeof(T) == 4) {
+    if (p->wTC) return tc_synthesis(p->dQ32, p->L, Y, p->dpsi32[j], Lb, cs, flm, p->wTC, p->tc_bytes, st);
+  }
+  const int mchunk = 16;
+  dim3 g((Lb + 31) / 32, (cs.Mc + 31) / 32, (Lb + mchunk - 1) / mchunk);
+  contract_synthesis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, Y, psi_of<T>(p, j), Lb, cs, mchunk, flm);
+  count_launch();
+  return launch_ok("contract_synthesis_kernel");
+}
+
+template <class T, class WT>
+static bool analysis_from_flm(crv_plan_s* p, const cx<double>* flm, void* const* W, size_t bidx, double* Wphi,
+                              cudaStream_t st) {
+  for (int j = p->J0; j <= p->J; ++j) {
+    const int Lb = p->Lj[j], N = 2 * Lb - 1;
+    const size_t we = (size_t)Lb * N * N * (p->real ? 1 : 2);
+    if (!W[j]) { g_err = "W[j] is NULL for a computed scale"; return false; }
+    if (!wigner_analysis_scale<T, WT>(p, j, flm, (WT*)W[j] + bidx * we, st)) return false;
+  }
+  if (Wphi) {
+    const int Lp = p->Lphi;
+    scaling_apply_kernel<<<(Lp * Lp + 255) / 256, 256, 0, st>>>(p->dphi, Lp, flm, p->wflm2, false);
+    count_launch();
+    if (!launch_ok("scaling_apply_kernel")) return false;
+    const size_t pe = (size_t)Lp * (2 * Lp - 1) * (p->real ? 1 : 2);
+    if (!sht_inverse(p, p->wflm2, Wphi + bidx * pe, Lp, 0, p->real, st)) return false;
+  }
+  return true;
+}
+
+template <class T, class WT>
+static bool synthesis_to_flm(crv_plan_s* p, const void* const* W, size_t bidx, const double* Wphi, cx<double>* flm,
+                             cudaStream_t st) {
+  cudaMemsetAsync(flm, 0, sizeof(cx<double>) * p->L * p->L, st);
+  for (int j = p->J0; j <= p->J; ++j) {
+    const int Lb = p->Lj[j], N = 2 * Lb - 1;
+    const size_t we = (size_t)Lb * N * N * (p->real ? 1 : 2);
+    if (!W[j]) { g_err = "W[j] is NULL for a computed scale"; return false; }
+    if (!wigner_synthesis_scale<T, WT>(p, j, (const WT*)W[j] + bidx * we, flm, st)) return false;
+  }
+  if (Wphi) {
+    const int Lp = p->Lphi;
+    const size_t pe = (size_t)Lp * (2 * Lp - 1) * (p->real ? 1 : 2);
+    if (!sht_forward(p, Wphi + bidx * pe, p->wflm2, Lp, 0, p->real, st)) return false;
+    scaling_apply_kernel<<<(Lp * Lp + 255) / 256, 256, 0, st>>>(p->dphi, Lp, p->wflm2, flm, true);
+    count_launch();
+    if (!launch_ok("scaling_apply_kernel")) return false;
+  }
+  flm_finish_kernel<<<(p->L * p->L + 255) / 256, 256, 0, st>>>(flm, p->L, p->spin, p->real);
+  count_launch();
+  return launch_ok("flm_finish_kernel");
+}
+
+// precision dispatch
+static bool do_analysis(crv_plan_s* p, const cx<double>* flm, void* const* W, size_t b, double* Wphi, cudaStream_t st) {
+  if (p->mixed) return p->wfp32 ? analysis_from_flm<float, float>(p, flm, W, b, Wphi, st)
+                                : analysis_from_flm<float, double>(p, flm, W, b, Wphi, st);
+  return p->wfp32 ? analysis_from_flm<double, float>(p, flm, W, b, Wphi, st)
+                  : analysis_from_flm<double, double>(p, flm, W, b, Wphi, st);
+}
+static bool do_synthesis(crv_plan_s* p, const void* const* W, size_t b, const double* Wphi, cx<double>* flm,
+                         cudaStream_t st) {
+  if (p->mixed) return p->wfp32 ? synthesis_to_flm<float, float>(p, W, b, Wphi, flm, st)
+                                : synthesis_to_flm<float, double>(p, W, b, Wphi, flm, st);
+  return p->wfp32 ? synthesis_to_flm<double, float>(p, W, b, Wphi, flm, st)
+                  : synthesis_to_flm<double, double>(p, W, b, Wphi, flm, st);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* crv_last_error(void) { return g_err.c_str(); }
+
+const char* crv_status_string(int s) {
+  switch (s) {
+    case CRV_OK: return "CRV_OK";
+    case CRV_EINVAL: return "CRV_EINVAL";
+    case CRV_ENOMEM: return "CRV_ENOMEM";
+    case CRV_ECUDA: return "CRV_ECUDA";
+    case CRV_ETIMEOUT: return "CRV_ETIMEOUT";
+    case CRV_EUNSUPPORTED: return "CRV_EUNSUPPORTED";
+    default: return "unknown status";
+  }
+}
+
+unsigned long long crv_launch_count(void) { return g_launches.load(); }
+
+int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule, unsigned flags,
+                    int max_batch, void* stream) {
+  if (!out) return fail(CRV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (L < 2 || L > 4096) return fail(CRV_EINVAL, "L must be in [2, 4096]");
+  if (!(lambda > 1.0) || !std::isfinite(lambda)) return fail(CRV_EINVAL, "lambda must be > 1");
+  if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
+  if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");
+  if (nrule != CRV_NRULE_CURVELET) return fail(CRV_EINVAL, "unknown nrule");
+  if (flags & ~7u) return fail(CRV_EINVAL, "unknown flag bits");
+  if ((flags & CRV_F_REAL) && spin != 0) return fail(CRV_EINVAL, "CRV_F_REAL requires spin 0");
+  if (max_batch < 1) return fail(CRV_EINVAL, "max_batch must be >= 1");
+  int J = 0;
+  while (std::pow(lambda, J) < L * (1 - 1e-14)) ++J;
+  if (J > 64) return fail(CRV_EINVAL, "lambda too close to 1 (more than 64 scales)");
+  if (J0 > J) return fail(CRV_EINVAL, "J0 exceeds the largest scale J");
+  if (std::pow(lambda, J0) < std::abs(spin) * (1 - 1e-14))
+    return fail(CRV_EINVAL, "lambda^J0 < |spin|: vartheta^j = arccos(-s/lambda^j) undefined");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(CRV_EUNSUPPORTED, "no CUDA device");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* p = new crv_plan_s();
+  p->L = L; p->lambda = lambda; p->J0 = J0; p->J = J; p->spin = spin; p->flags = flags; p->max_batch = max_batch;
+  p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
+  p->Lphi = std::max(1, ceil_pow(lambda, J0));
+  p->Lphi = std::min(p->Lphi, L);
+  p->Lj.assign(J + 1, 0);
+  for (int j = J0; j <= J; ++j) p->Lj[j] = std::min(L, ceil_pow(lambda, j + 1));
+  // kernels (Sec. II-B)
+  KLambda k(lambda);
+  p->kappa.assign((size_t)(J + 1) * L, 0.0);
+  for (int j = J0; j <= J; ++j)
+    for (int l = 0; l < L; ++l) {
+      double v = k(l / std::pow(lambda, j + 1)) - k(l / std::pow(lambda, j));
+      p->kappa[(size_t)j * L + l] = v > 0 ? std::sqrt(v) : 0.0;
+    }
+  p->phi.assign(L, 0.0);
+  for (int l = 0; l < L; ++l) p->phi[l] = std::sqrt(k(l / std::pow(lambda, J0)));
+  p->psi.assign(J + 1, {});
+  std::vector<double> dp, dm;
+  for (int j = J0; j <= J; ++j) {
+    const int Lb = p->Lj[j], N = 2 * Lb - 1;
+    std::vector<double>& ps = p->psi[j];
+    ps.assign((size_t)Lb * N, 0.0);
+    const double th = std::acos(-spin / std::pow(lambda, j));
+    const double sh = spin == 0 ? std::sqrt(0.5) : std::sin(th / 2), ch = spin == 0 ? std::sqrt(0.5) : std::cos(th / 2);
+    for (int l = std::abs(spin); l < Lb; ++l) {
+      const double fac = std::sqrt((2.0 * l + 1) / (8 * M_PI * M_PI)) * p->kappa[(size_t)j * L + l];
+      if (fac == 0.0) continue;
+      if (l == 0) { ps[Lb - 1] = fac / std::sqrt(2.0); continue; }
+      // zeta_lk = (d^l_{k,l}(t) + (-1)^l d^l_{k,-l}(t))/sqrt2, d^l_{k,-l} = (-1)^{l-k} d^l_{-k,l}
+      edge_row(l, sh, ch, dp);
+      for (int kk = -l; kk <= l; ++kk) {
+        if (spin == 0 && (kk & 1)) continue;  // exact zeros at vartheta = pi/2
+        double dneg = dp[-kk + l] * (((l - kk) & 1) ? -1.0 : 1.0);
+        double z = (dp[kk + l] + ((l & 1) ? -dneg : dneg)) / std::sqrt(2.0);
+        ps[(size_t)l * N + (kk + Lb - 1)] = fac * z;
+      }
+    }
+  }
+  int stt = CRV_OK;
+  // device tables
+  const size_t n3 = (size_t)L * L * L;
+  p->dQ = p->dalloc<double>(n3, &stt);
+  if (p->mixed) p->dQ32 = p->dalloc<float>(n3, &stt);
+  p->dpsi.assign(J + 1, nullptr);
+  p->dpsi32.assign(J + 1, nullptr);
+  for (int j = J0; j <= J && stt == CRV_OK; ++j) {
+    const size_t ne = p->psi[j].size();
+    p->dpsi[j] = p->dalloc<double>(ne, &stt);
+    p->dpsi32[j] = p->dalloc<float>(ne, &stt);
+    if (stt != CRV_OK) break;
+    std::vector<float> f32(p->psi[j].begin(), p->psi[j].end());
+    cudaMemcpy(p->dpsi[j], p->psi[j].data(), ne * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->dpsi32[j], f32.data(), ne * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  p->dphi = p->dalloc<double>(L, &stt);
+  if (stt == CRV_OK) cudaMemcpy(p->dphi, p->phi.data(), L * sizeof(double), cudaMemcpyHostToDevice);
+  // FFT tables for every band limit in use
+  std::set<int> lbs = {L, p->Lphi};
+  for (int j = J0; j <= J; ++j) lbs.insert(p->Lj[j]);
+  for (int lb : lbs)
+    if (stt == CRV_OK) stt = build_fft(p, lb);
+  // workspace
+  const int Mc = p->mc(L), Nc = p->nc(L), N = 2 * L - 1;
+  const size_t el = p->mixed ? sizeof(cx<float>) : sizeof(cx<double>);
+  p->vol_bytes = (size_t)L * Mc * Nc * el;
+  p->wflm = p->dalloc<cx<double>>((size_t)L * L, &stt);
+  p->wflm2 = p->dalloc<cx<double>>((size_t)L * L, &stt);
+  p->wF = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
+  p->wG = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
+  p->wX = p->dalloc<unsigned char>(p->vol_bytes, &stt);
+  p->wXb = p->dalloc<unsigned char>(p->vol_bytes, &stt);
+  {
+    // ring-chunk buffer: at least one ring, at most all rings, about 96 MB (L2-resident)
+    const size_t one = (size_t)N * std::max(Mc, Nc) * el;
+    p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)96 << 20));
+  }
+  p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
+  if (p->mixed && stt == CRV_OK) {
+    p->tc_bytes = tc_scratch_bytes(L, Mc, Nc);
+    if (p->tc_bytes) p->wTC = p->dalloc<unsigned char>(p->tc_bytes, &stt);
+  }
+  if (stt != CRV_OK) { delete p; return stt; }
+  // Delta tables
+  double* seed_v = nullptr;
+  int* seed_e = nullptr;
+  if (cudaMalloc(&seed_v, sizeof(double) * (size_t)L * L) != cudaSuccess ||
+      cudaMalloc(&seed_e, sizeof(int) * (size_t)L * L) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(seed_v);
+    delete p;
+    return fail(CRV_ENOMEM, "seed table allocation failed");
+  }
+  cudaError_t e = build_delta(L, p->dQ, p->dQ32, seed_v, seed_e, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(seed_v);
+  cudaFree(seed_e);
+  if (e != cudaSuccess) {
+    std::string m = std::string("Delta table build failed: ") + cudaGetErrorString(e) + " " + g_err;
+    delete p;
+    return fail(CRV_ECUDA, m);
+  }
+  *out = p;
+  return CRV_OK;
+}
+
+int crv_plan_destroy(crv_plan_t p) {
+  if (!p) return CRV_OK;
+  cudaDeviceSynchronize();
+  delete p;
+  return CRV_OK;
+}
+
+int crv_plan_info(crv_plan_t p, int* J, int* Lj, size_t* w_elems, int* L_phi, size_t* workspace_bytes) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (J) *J = p->J;
+  for (int j = 0; j <= p->J; ++j) {
+    const int Lb = p->Lj[j];
+    if (Lj) Lj[j] = (j >= p->J0) ? Lb : 0;
+    if (w_elems) w_elems[j] = (j >= p->J0) ? (size_t)Lb * (2 * Lb - 1) * (2 * Lb - 1) : 0;
+  }
+  if (L_phi) *L_phi = p->Lphi;
+  if (workspace_bytes) *workspace_bytes = p->bytes;
+  return CRV_OK;
+}
+
+int crv_plan_kernel(crv_plan_t p, int j, double* out) {
+  if (!p || !out) return fail(CRV_EINVAL, "null argument");
+  if (j < p->J0 || j > p->J) return fail(CRV_EINVAL, "scale out of range");
+  std::memcpy(out, p->psi[j].data(), p->psi[j].size() * sizeof(double));
+  return CRV_OK;
+}
+
+int crv_plan_scaling(crv_plan_t p, double* out) {
+  if (!p || !out) return fail(CRV_EINVAL, "null argument");
+  std::memcpy(out, p->phi.data(), p->phi.size() * sizeof(double));
+  return CRV_OK;
+}
+
+int crv_plan_delta(crv_plan_t p, int l, double* out) {
+  if (!p || !out) return fail(CRV_EINVAL, "null argument");
+  if (l < 0 || l >= p->L) return fail(CRV_EINVAL, "l out of range");
+  const size_t L = p->L;
+  cudaError_t e = cudaMemcpy2D(out, (l + 1) * sizeof(double), p->dQ + (size_t)l * L, L * L * sizeof(double),
+                               (l + 1) * sizeof(double), l + 1, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
+  return CRV_OK;
+}
+
+static int check_batch(crv_plan_t p, int B, const void* a, const void* b) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (B < 0 || B > p->max_batch) return fail(CRV_EINVAL, "B must be in [0, max_batch]");
+  if (B > 0 && (!a || !b)) return fail(CRV_EINVAL, "null data pointer");
+  return CRV_OK;
+}
+
+int crv_sht_fwd(crv_plan_t p, const void* map, void* flm, int B, void* stream) {
+  int s = check_batch(p, B, map, flm);
+  if (s) return s;
+  const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
+  for (int b = 0; b < B; ++b)
+    if (!sht_forward(p, (const double*)map + b * me, (cx<double>*)flm + (size_t)b * p->L * p->L, p->L, p->spin,
+                     p->real, (cudaStream_t)stream))
+      return CRV_ECUDA;
+  return CRV_OK;
+}
+
+int crv_sht_inv(crv_plan_t p, const void* flm, void* map, int B, void* stream) {
+  int s = check_batch(p, B, flm, map);
+  if (s) return s;
+  const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
+  for (int b = 0; b < B; ++b)
+    if (!sht_inverse(p, (const cx<double>*)flm + (size_t)b * p->L * p->L, (double*)map + b * me, p->L, p->spin,
+                     p->real, (cudaStream_t)stream))
+      return CRV_ECUDA;
+  return CRV_OK;
+}
+
+int crv_analysis_lm(crv_plan_t p, const void* flm, void* const* W, void* Wphi, int B, void* stream) {
+  int s = check_batch(p, B, flm, W);
+  if (s) return s;
+  for (int b = 0; b < B; ++b)
+    if (!do_analysis(p, (const cx<double>*)flm + (size_t)b * p->L * p->L, W, b, (double*)Wphi, (cudaStream_t)stream))
+      return CRV_ECUDA;
+  return CRV_OK;
+}
+
+int crv_analysis(crv_plan_t p, const void* map, void* const* W, void* Wphi, int B, void* stream) {
+  int s = check_batch(p, B, map, W);
+  if (s) return s;
+  const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
+  for (int b = 0; b < B; ++b) {
+    if (!sht_forward(p, (const double*)map + b * me, p->wflm, p->L, p->spin, p->real, (cudaStream_t)stream))
+      return CRV_ECUDA;
+    if (!do_analysis(p, p->wflm, W, b, (double*)Wphi, (cudaStream_t)stream)) return CRV_ECUDA;
+  }
+  return CRV_OK;
+}
+
+int crv_synthesis_lm(crv_plan_t p, const void* const* W, const void* Wphi, void* flm, int B, void* stream) {
+  int s = check_batch(p, B, W, flm);
+  if (s) return s;
+  for (int b = 0; b < B; ++b)
+    if (!do_synthesis(p, W, b, (const double*)Wphi, (cx<double>*)flm + (size_t)b * p->L * p->L, (cudaStream_t)stream))
+      return CRV_ECUDA;
+  return CRV_OK;
+}
+
+int crv_synthesis(crv_plan_t p, const void* const* W, const void* Wphi, void* map, int B, void* stream) {
+  int s = check_batch(p, B, W, map);
+  if (s) return s;
+  const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
+  for (int b = 0; b < B; ++b) {
+    if (!do_synthesis(p, W, b, (const double*)Wphi, p->wflm, (cudaStream_t)stream)) return CRV_ECUDA;
+    if (!sht_inverse(p, p->wflm, (double*)map + b * me, p->L, p->spin, p->real, (cudaStream_t)stream)) return CRV_ECUDA;
+  }
+  return CRV_OK;
+}
+
+}  // extern "C"

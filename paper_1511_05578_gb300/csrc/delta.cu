@@ -1,0 +1,107 @@
+// Delta^l_{mn} = d^l_mn(pi/2) tables (Sec. III-A-2, the matrices behind the
+// factorisation d^l_mn(beta) = i^{n-m} sum_m' Delta^l_{m'm} Delta^l_{m'n} e^{i m' beta}).
+//
+// Stored as the quarter table Q[m'][l][n] = Delta^l_{m'n} for 0 <= m', n <= l < L
+// (dense L^3, zero where l < max(m', n)); the other quadrants follow from
+// Delta^l_{-m',n} = (-1)^{l+n} Delta^l_{m'n} and Delta^l_{m',-n} = (-1)^{l+m'} Delta^l_{m'n}.
+//
+// Recursion (Trapani-Navaza form, FP64):
+//   edge row   Delta^l_{l,n} = (-1)^{l-n} 2^{-l} sqrt(C(2l, l+n))
+//              (the single surviving term of Eq. wigner_sum_reln at beta = pi/2),
+//              built per l by the ratio Delta^l_{l,n+1}/Delta^l_{l,n} = -sqrt((l-n)/(l+n+1))
+//              from 2^{-l} sqrt(C(2l,l)) = prod_k sqrt((2k-1)/(2k));
+//   columns    Delta^l_{m,n} = 2n/sqrt((l-m)(l+m+1)) Delta^l_{m+1,n}
+//                - sqrt((l-m-1)(l+m+2)/((l-m)(l+m+1))) Delta^l_{m+2,n},  m = l-1 .. 0.
+// The edge values reach 2^-l, below the double range past l ~ 1022, so every value
+// carries its own binary exponent until it is stored (values that are still below
+// the double range then flush to zero, where they contribute nothing).
+#include "common.cuh"
+
+namespace crv {
+
+// One thread per l: seed row (mantissa, exponent) for n = 0..l.
+__global__ void delta_seed_kernel(int L, double* __restrict__ seed_v, int* __restrict__ seed_e) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double v = 1.0;
+  int e = 0;
+  for (int k = 1; k <= l; ++k) {  // 2^-l sqrt(C(2l, l)) = prod sqrt((2k-1)/(2k)), stays > 0.05 for l <= 4096
+    v *= sqrt((2.0 * k - 1.0) / (2.0 * k));
+  }
+  if (l & 1) v = -v;  // (-1)^{l-n} at n = 0
+  for (int n = 0; n <= l; ++n) {
+    seed_v[(size_t)l * L + n] = v;
+    seed_e[(size_t)l * L + n] = e;
+    if (n < l) {
+      v = -v * sqrt((double)(l - n) / (double)(l + n + 1));
+      int k;
+      v = frexp(v, &k);
+      e += k;
+    }
+  }
+}
+
+// Block per (l, 128 consecutive n). Writes Q (double) and, if q32 != null, a float copy.
+__global__ void __launch_bounds__(128) delta_column_kernel(int L, const double* __restrict__ seed_v,
+                                                           const int* __restrict__ seed_e, double* __restrict__ Q,
+                                                           float* __restrict__ q32) {
+  extern __shared__ double coef[];  // [2*l]: a[m], b[m] for m < l
+  const int l = blockIdx.y;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x * blockDim.x > l) return;  // whole block beyond the row
+  for (int m = threadIdx.x; m < l; m += blockDim.x) {
+    const double den = (double)(l - m) * (double)(l + m + 1);
+    const double a = 1.0 / sqrt(den);
+    coef[m] = a;
+    coef[l + m] = (m + 1 < l) ? sqrt((double)(l - m - 1) * (double)(l + m + 2)) * a : 0.0;
+  }
+  __syncthreads();
+  if (n > l) return;
+  const size_t LL = (size_t)L * L;
+  double v1 = seed_v[(size_t)l * L + n], v2 = 0.0;  // Delta_{m+1,n}, Delta_{m+2,n}
+  int e = seed_e[(size_t)l * L + n];
+  auto store = [&](int m, double v) {
+    const double t = (e < -2000) ? 0.0 : ldexp(v, e);
+    const size_t idx = (size_t)m * LL + (size_t)l * L + n;
+    Q[idx] = t;
+    if (q32) q32[idx] = (float)t;
+  };
+  store(l, v1);
+  const double twon = 2.0 * n;
+  for (int m = l - 1; m >= 0; --m) {
+    const double v = twon * coef[m] * v1 - coef[l + m] * v2;
+    v2 = v1;
+    v1 = v;
+    if (fabs(v1) > 0x1p600) {
+      v1 = ldexp(v1, -600);
+      v2 = ldexp(v2, -600);
+      e += 600;
+    }
+    store(m, v1);
+  }
+}
+
+cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_e, cudaStream_t st) {
+  const size_t n3 = (size_t)L * L * L;
+  cudaError_t err = cudaMemsetAsync(Q, 0, n3 * sizeof(double), st);
+  if (err != cudaSuccess) return err;
+  if (q32) {
+    err = cudaMemsetAsync(q32, 0, n3 * sizeof(float), st);
+    if (err != cudaSuccess) return err;
+  }
+  delta_seed_kernel<<<(L + 127) / 128, 128, 0, st>>>(L, seed_v, seed_e);
+  count_launch();
+  if (!launch_ok("delta_seed_kernel")) return cudaErrorLaunchFailure;
+  const size_t smem = sizeof(double) * 2 * (size_t)L;
+  if (smem > 48 * 1024) {
+    err = cudaFuncSetAttribute(delta_column_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+  }
+  dim3 grid((L + 127) / 128, L);
+  delta_column_kernel<<<grid, 128, smem, st>>>(L, seed_v, seed_e, Q, q32);
+  count_launch();
+  if (!launch_ok("delta_column_kernel")) return cudaErrorLaunchFailure;
+  return cudaSuccess;
+}
+
+}  // namespace crv

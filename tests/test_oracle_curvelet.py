@@ -113,7 +113,7 @@ def test_analysis_against_brute_force(lam, J0, s, L, real):
             if real:
                 assert np.abs(W[j][b].imag).max() < 1e-14
     # scaling map: inverse spin-0 SHT of sqrt(k(l/lam^J0)) f_lm (Eq. analysis_scaling_harmonic)
-    Lp = O.L_phi(lam, J0)
+    Lp = O.L_phi(lam, J0, L)
     th, ph = O.mw_theta(Lp), O.mw_phi(Lp)
     want = np.zeros((Lp, 2 * Lp - 1), dtype=np.complex128)
     for l in range(min(Lp, L)):
