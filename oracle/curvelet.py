@@ -52,6 +52,8 @@ def lib():
         h.orc_d_edge.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         h.orc_d_edge_row.restype = None
         h.orc_d_edge_row.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        h.orc_k_diff.restype = ctypes.c_double
+        h.orc_k_diff.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         h.orc_k_lambda.restype = ctypes.c_double
         h.orc_k_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib = h
@@ -225,10 +227,14 @@ def L_phi(lam, J0, L=None):
 
 
 def kappa(lam, j, L):
-    """kappa^(j)(l) = kappa_lambda(lam^-j l) = sqrt(k(l/lam^(j+1)) - k(l/lam^j)), l < L."""
-    l = np.arange(L, dtype=np.float64)
-    v = k_lambda(lam, l / lam ** (j + 1)) - k_lambda(lam, l / lam ** j)
-    return np.sqrt(np.maximum(v, 0.0))
+    """kappa^(j)(l) = kappa_lambda(lam^-j l) = sqrt(k(l/lam^(j+1)) - k(l/lam^j)), l < L.
+    The difference is evaluated as one integral over the gap between the two
+    arguments (same quantity; avoids cancellation next to the support ends)."""
+    h = lib()
+    out = np.zeros(L)
+    for l in range(L):
+        out[l] = math.sqrt(max(h.orc_k_diff(float(lam), l / lam ** (j + 1), l / lam ** j), 0.0))
+    return out
 
 
 def phi_scaling(lam, J0, L):

@@ -436,6 +436,14 @@ static double integrate_k(double lam, double a, double b) {
   }
   return acc;
 }
+/* k_lambda(a) - k_lambda(b) for a <= b, as one normalised integral over
+ * [max(a, 1/lambda), min(b, 1)] (no cancellation where the two are close). */
+double orc_k_diff(double lam, double a, double b) {
+  double lo = a < 1.0 / lam ? 1.0 / lam : a, hi = b > 1.0 ? 1.0 : b;
+  if (hi <= lo) return 0.0;
+  return integrate_k(lam, lo, hi) / integrate_k(lam, 1.0 / lam, 1.0);
+}
+
 double orc_k_lambda(double lam, double t) {
   if (t < 1.0 / lam) return 1.0;
   if (t >= 1.0) return 0.0;

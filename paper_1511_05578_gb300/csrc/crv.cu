@@ -88,6 +88,12 @@ struct KLambda {
     if (t >= 1) return 0.0;
     return integral(t, 1) / norm;
   }
+  // k(a) - k(b), a <= b, as one integral over [max(a,1/lam), min(b,1)]: no
+  // cancellation next to the ends of the support, where kappa^2 is tiny.
+  double diff(double a, double b) const {
+    const double lo = std::max(a, 1 / lam), hi = std::min(b, 1.0);
+    return hi > lo ? integral(lo, hi) / norm : 0.0;
+  }
 };
 
 static int ceil_pow(double lam, int e) {
@@ -583,7 +589,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->kappa.assign((size_t)(J + 1) * L, 0.0);
   for (int j = J0; j <= J; ++j)
     for (int l = 0; l < L; ++l) {
-      double v = k(l / std::pow(lambda, j + 1)) - k(l / std::pow(lambda, j));
+      double v = k.diff(l / std::pow(lambda, j + 1), l / std::pow(lambda, j));
       p->kappa[(size_t)j * L + l] = v > 0 ? std::sqrt(v) : 0.0;
     }
   p->phi.assign(L, 0.0);

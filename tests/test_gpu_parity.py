@@ -47,7 +47,8 @@ def test_plan_kernels_match_oracle(lam, J0, s, L):
     assert np.abs(p.scaling() - O.phi_scaling(lam, J0, L)).max() < 1e-13
     for j in range(J0, p.J + 1):
         assert p.Lj[j] == O.band_limit(lam, j, L)
-        assert np.abs(p.kernel(j) - O.psi(lam, j, s, p.Lj[j])).max() < 1e-13, j
+        # two evaluations of the same closed form; rounding grows ~linearly in l
+        assert np.abs(p.kernel(j) - O.psi(lam, j, s, p.Lj[j])).max() < 1e-13 + 1e-14 * p.Lj[j], j
     p.close()
 
 
