@@ -1,0 +1,472 @@
+#!/usr/bin/env python3
+"""Benchmark: curvelet analysis + synthesis throughput (maps/s) on one or more GPUs.
+
+Workload (default): 32 real spin-0 maps per GPU, band limit L = 1024, lambda = 2,
+J0 = 2, mixed precision (split-FP32 contraction, FP32 FFTs and W storage; FP64
+Delta tables and FP64 f_lm accumulation). One step = for every map: forward SHT ->
+curvelet analysis onto all SO(3) scale grids (W materialised in HBM) -> synthesis
+-> inverse SHT. Inputs are seeded synthetic band-limited maps (Gaussian f_lm with
+C_l = (l+1)^-2, seed 1000*2 + map index), 16.8 MB each, so one step's inputs (537 MB)
+exceed the 126 MB L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--L 1024] [--B 32]
+                  [--mode mixed|fp64] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun each rank runs its own 32 maps
+(independent problems: weak scaling, no data-path collective); value = all ranks'
+maps / max-over-ranks time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "maps/s analysis+synthesis at L=1024, mixed vs FP64 (err<=1e-5); p50/p99 ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--L", type=int, default=1024)
+    ap.add_argument("--B", type=int, default=32)
+    ap.add_argument("--lam", type=float, default=2.0)
+    ap.add_argument("--J0", type=int, default=2)
+    ap.add_argument("--mode", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-sample-maps", type=int, default=1,
+                    help="maps timed on the plain FP64 path for the mixed/FP64 speedup (0 = skip)")
+    ap.add_argument("--breakdown", action="store_true", help="print per-kernel-kind device time to stderr")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per map (for the roofline object)
+# ---------------------------------------------------------------------------
+def plan_shapes(L, lam, J0, real=True, spin=0):
+    J = 0
+    while lam ** J < L * (1 - 1e-14):
+        J += 1
+    out = []
+    for j in range(J0, J + 1):
+        v = lam ** (j + 1)
+        r = round(v)
+        Lb = min(L, int(r) if abs(v - r) < 1e-9 * max(1, v) else int(math.ceil(v)))
+        N = 2 * Lb - 1
+        Mc = Lb if real else N
+        if spin == 0:
+            n0 = -(Lb - 1) + ((Lb - 1) % 2)
+            Nc = (-n0 - n0) // 2 + 1
+        else:
+            Nc = N
+        out.append((j, Lb, N, Mc, Nc))
+    return J, out
+
+
+def contraction_terms(Lb, real=True, spin=0):
+    """Number of (l, m, n, m'>=0) terms of the Delta contraction of one scale."""
+    tot = 0
+    for l in range(Lb):
+        nm = (l + 1) if real else (2 * l + 1)       # m in the m-set with |m| <= l
+        nn = 2 * (l // 2) + 1 if spin == 0 else 2 * l + 1  # even n (spin 0) with |n| <= l
+        tot += (l + 1) * nm * nn                     # m' = 0..l
+    return tot
+
+
+def kind_work(L, lam, J0, el_bytes, w_bytes):
+    """Algorithmic bytes (input read + output written, once) and flops per map for each
+    kernel kind of the Wigner pipelines."""
+    J, shapes = plan_shapes(L, lam, J0)
+    w = {}
+
+    def add(k, b=0.0, f=0.0):
+        B0, F0 = w.get(k, (0.0, 0.0))
+        w[k] = (B0 + b, F0 + f)
+    for (j, Lb, N, Mc, Nc) in shapes:
+        vol = Lb * Mc * Nc * el_bytes           # X, Xb, Y volumes (complex)
+        ring_t = Lb * Mc * N * el_bytes         # T after the n -> gamma step
+        ring_u = Lb * N * Nc * el_bytes         # U after the gamma -> n step
+        wv = Lb * N * N * w_bytes               # W_j
+        terms = contraction_terms(Lb)
+        add("contract_analysis", vol, 4.0 * terms)
+        add("tc_analysis", vol, 4.0 * terms)
+        add("beta_synth", 2 * vol)
+        add("ring_inv_n", vol + ring_t)
+        add("ring_inv_m", ring_t + wv)
+        add("ring_fwd_g", wv + ring_u)
+        add("ring_fwd_a", ring_u + vol)
+        add("beta_quad", 2 * vol)
+        add("contract_synthesis", vol, 4.0 * terms)
+        add("tc_synthesis", vol, 4.0 * terms)
+    return w
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs"), "bf16_tflops": d.get("bf16_tflops"),
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flop per FMA at the sampled SM clock
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
+def fp64_alu_peak_tflops(sm_mhz):
+    # FP64 FMA rate measured on this machine: 1.01 TFLOP/s at 1995 MHz (0.5 lane-FMA/clk/SM x 64)
+    return 1.0124 * (sm_mhz or 1995.0) / 1995.0
+
+
+# ---------------------------------------------------------------------------
+# the oracle arm (CPU)
+# ---------------------------------------------------------------------------
+def oracle_maps_per_s(L, lam, J0, rings_per_sample=1, seed=2000):
+    """Time the FP64 oracle's curvelet analysis on sampled rings of the top scale and
+    extrapolate to one full map round trip: analysis cost per ring scales as L_j^3
+    (Risbo recursion at beta_b plus the per-ring sums), summed over all rings of all
+    scales; synthesis is taken as equal to analysis (its adjoint, same order of work);
+    the two O(L^3) SHTs are left out (under 1% here)."""
+    import numpy as np
+    import oracle as O
+    from paper_1511_05578_gb300 import inputs
+    f = inputs.flm_gaussian(L, seed, real=True)
+    J = O.J_max(lam, L)
+    Lt = O.band_limit(lam, J, L)
+    ps = O.psi(lam, J, 0, Lt)
+    rings = list(np.linspace(0, Lt - 1, rings_per_sample + 2).astype(int)[1:-1])
+    t0 = time.perf_counter()
+    O.analysis_rings(f, lam, J, 0, L, rings=rings, psi_j=ps)
+    dt = (time.perf_counter() - t0) / len(rings)
+    total = 0.0
+    for j in range(J0, J + 1):
+        Lb = O.band_limit(lam, j, L)
+        total += Lb * dt * (Lb / Lt) ** 3
+    per_map = 2.0 * total
+    return 1.0 / per_map, {"ring_s": dt, "rings": len(rings), "per_map_s": per_map}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    # the oracle runs on rank 0 only
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_maps_per_s(args.L, args.lam, args.J0, 1)
+    for _ in range(args.steps):
+        v, info = oracle_maps_per_s(args.L, args.lam, args.J0, 1)
+        vals.append(v)
+    v = sorted(vals)[len(vals) // 2]
+    sample = (f"1 ring of the top scale (L_j={args.L}) per step, extrapolated by L_j^3 over all rings of all "
+              f"scales, synthesis = analysis; {info['ring_s']:.2f} s per ring")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "maps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * args.B / v,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args),
+        "cpu_baseline": {"value": v, "unit": "maps/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": f"curvelet analysis+synthesis, {args.B} real spin-0 maps, L={args.L}, lambda={args.lam:g}, "
+                        f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}",
+            "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
+            "precision": args.mode, "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1511_05578_gb300 as crv
+    from paper_1511_05578_gb300 import build, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    L, lam, J0, B = args.L, args.lam, args.J0, args.B
+    flags = crv.CRV_F_REAL | (crv.CRV_F_MIXED | crv.CRV_F_W_FP32 if args.mode == "mixed" else 0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = crv.Plan(L, lam, J0, 0, flags, max_batch=1, stream=stream.cuda_stream)
+        # seeded inputs: f_lm on the host -> maps through our inverse SHT (not timed)
+        maps = torch.empty((B, L, 2 * L - 1), dtype=torch.float64, device="cuda")
+        f1 = plan.flm_tensor(1)
+        for b in range(B):
+            f1.copy_(torch.from_numpy(inputs.flm_gaussian(L, inputs.seed_for(2, rank * B + b), real=True)[None]))
+            crv.crv_sht_inv(plan.handle, f1, maps[b:b + 1], 1, stream.cuda_stream)
+        out = torch.empty_like(maps)
+        W = plan.W_tensors(1)
+        Wphi = plan.Wphi_tensor(1)
+    torch.cuda.synchronize()
+
+    def step(src, dst):
+        for b in range(B):
+            crv.crv_analysis(plan.handle, src[b:b + 1], W, Wphi, 1, stream.cuda_stream)
+            crv.crv_synthesis(plan.handle, W, Wphi, dst[b:b + 1], 1, stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(maps, out)
+    torch.cuda.synchronize()
+    # accuracy of the round trip on this rank's last map (FP32 W / mixed: <= 1e-5 relative)
+    recon = float(torch.linalg.vector_norm(out[-1] - maps[-1]) / torch.linalg.vector_norm(maps[-1]))
+
+    kinds = crv.crv_profile_kinds()
+    crv.crv_profile_reset()
+    crv.crv_profile_enable((1 << len(kinds)) - 1)
+    l0 = crv.crv_launch_count()
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per_step = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(maps, out)
+        b_.record(stream)
+        per_step.append((a, b_))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = crv.crv_launch_count() - l0
+    crv.crv_profile_enable(0)
+    ms_total = ev0.elapsed_time(ev1)
+    step_ms = [a.elapsed_time(b_) for a, b_ in per_step]
+    kind_ms = {}
+    kind_n = {}
+    for k, name in enumerate(kinds):
+        n, t = crv.crv_profile_read(k)
+        if n:
+            kind_ms[name], kind_n[name] = t, n
+    t_max = ms_total
+    if world > 1:
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_per_step = t_max / args.steps
+    value = world * B * args.steps / (t_max / 1000.0)
+
+    # per-map latency (p50 / p99) from per-map events, one extra pass
+    lat = []
+    for b in range(B):
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        crv.crv_analysis(plan.handle, maps[b:b + 1], W, Wphi, 1, stream.cuda_stream)
+        crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + 1], 1, stream.cuda_stream)
+        b_.record(stream)
+        lat.append((a, b_))
+    torch.cuda.synchronize()
+    lat_ms = sorted(a.elapsed_time(b_) for a, b_ in lat)
+    p50 = lat_ms[len(lat_ms) // 2]
+    p99 = lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]
+
+    # end to end through the public API with host buffers (pinned), copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        host_in = maps.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        dev_in = torch.empty((1, L, 2 * L - 1), dtype=torch.float64, device="cuda")
+        dev_out = torch.empty_like(dev_in)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for b in range(B):
+                dev_in.copy_(host_in[b:b + 1], non_blocking=True)
+                crv.crv_analysis(plan.handle, dev_in, W, Wphi, 1, stream.cuda_stream)
+                crv.crv_synthesis(plan.handle, W, Wphi, dev_out, 1, stream.cuda_stream)
+                host_out[b:b + 1].copy_(dev_out, non_blocking=True)
+        stream.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        nb = B * L * (2 * L - 1) * 8
+        e2e = {"value": world * B / t_e2e, "unit": "maps/s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+    # plain FP64 GPU path on a sample of maps, for the mixed/FP64 speedup
+    fp64 = None
+    if args.mode == "mixed" and args.fp64_sample_maps > 0 and rank == 0:
+        del W
+        torch.cuda.empty_cache()
+        with torch.cuda.stream(stream):
+            p64 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL, max_batch=1, stream=stream.cuda_stream)
+            W64 = p64.W_tensors(1)
+            P64 = p64.Wphi_tensor(1)
+            o64 = torch.empty_like(maps[:1])
+        torch.cuda.synchronize()
+        crv.crv_analysis(p64.handle, maps[:1], W64, P64, 1, stream.cuda_stream)  # warm-up
+        crv.crv_synthesis(p64.handle, W64, P64, o64, 1, stream.cuda_stream)
+        torch.cuda.synchronize()
+        n64 = args.fp64_sample_maps
+        a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(n64):
+            crv.crv_analysis(p64.handle, maps[i:i + 1], W64, P64, 1, stream.cuda_stream)
+            crv.crv_synthesis(p64.handle, W64, P64, o64, 1, stream.cuda_stream)
+        b_.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b_) / n64
+        rec64 = float(torch.linalg.vector_norm(o64[0] - maps[n64 - 1]) / torch.linalg.vector_norm(maps[n64 - 1]))
+        fp64 = {"maps_per_s": 1000.0 / ms64, "ms_per_map": ms64, "sample_maps": n64,
+                "speedup_mixed_over_fp64": (1000.0 / ms64 and value / world / (1000.0 / ms64)),
+                "roundtrip_rel_l2": rec64}
+        p64.close()
+
+    # roofline of the dominant kernel kind
+    peaks = measured_peaks()
+    el = 8 if args.mode == "mixed" else 16
+    wb = 4 if args.mode == "mixed" else 8
+    work = kind_work(L, lam, J0, el, wb)
+    dom = max(kind_ms, key=kind_ms.get) if kind_ms else None
+    roof = None
+    if dom:
+        avg_ms = kind_ms[dom] / kind_n[dom]
+        per_launch_units = kind_n[dom] / (args.steps * B)  # launches of this kind per map
+        bytes_map, flops_map = work.get(dom, (0.0, 0.0))
+        if dom in ("contract_analysis", "contract_synthesis"):
+            flops_launch = flops_map / per_launch_units
+            peak = fp32_alu_peak_tflops(clk.get("sm_mhz")) if args.mode == "mixed" else fp64_alu_peak_tflops(clk.get("sm_mhz"))
+            ach = flops_launch / (avg_ms * 1e-3) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_src": "FP32 FMA lanes x clock" if args.mode == "mixed" else "FP64 FMA rate measured on this pool"}
+        elif dom in ("tc_analysis", "tc_synthesis"):
+            flops_launch = flops_map / per_launch_units
+            peak = peaks["bf16_tflops_sustained"] / 2.0  # TF32 = bf16 / 2 (nominal ratio)
+            ach = flops_launch / (avg_ms * 1e-3) / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_src": f"{peaks['src']} bf16 sustained / 2 (tf32); achieved counts FP32-accurate flops"}
+        else:
+            bytes_launch = bytes_map / per_launch_units
+            ach = bytes_launch / (avg_ms * 1e-3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_src": peaks["src"]}
+        roof["avg_launch_ms"] = avg_ms
+        roof["launches"] = kind_n[dom]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
+        "config": config_dict(args), "p50_ms": p50, "p99_ms": p99, "latency_unit": "ms per map (analysis+synthesis)",
+        "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "e2e": e2e,
+        "fp64_path": fp64, "step_ms": step_ms,
+        "kernels_ms_per_step": {k: v / args.steps for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = oracle_maps_per_s(L, lam, J0, 1)
+        line["cpu_baseline"] = {"value": v, "unit": "maps/s", "cores": cpu_cores(), "kind": "oracle",
+                                "sample": f"FP64 oracle analysis of 1 ring of the top scale (L_j={L}, "
+                                          f"{info['ring_s']:.2f} s), extrapolated by L_j^3 over all rings of all "
+                                          f"scales; synthesis taken equal to analysis"}
+    if args.breakdown and rank == 0:
+        for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1]):
+            sys.stderr.write(f"{k:20s} {v / args.steps:10.2f} ms/step  {kind_n[k] // args.steps:7d} launches/step\n")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,18 @@ const char* crv_status_string(int status);
  * threads). Used to count device work inside timed regions. */
 unsigned long long crv_launch_count(void);
 
+/* Optional per-kernel timing for measurement tools. When bit k of kind_mask is set,
+ * every launch of kernel kind k is bracketed by CUDA events recorded on the stream it
+ * is launched on; crv_profile_read waits for the recorded events and returns the
+ * launch count and summed device time (ms) of kind k since the last reset. Kinds are
+ * numbered 0 .. crv_profile_num_kinds()-1 and named by crv_profile_kind_name.
+ * Off by default; enabling it adds two event records per timed launch. */
+int crv_profile_enable(unsigned kind_mask);
+int crv_profile_num_kinds(void);
+const char* crv_profile_kind_name(int k);
+int crv_profile_read(int k, unsigned long long* launches, double* total_ms);
+int crv_profile_reset(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,8 @@ __all__ = [
     "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
     "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_last_error", "crv_status_string",
-    "crv_launch_count", "Plan",
+    "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
+    "Plan",
 ]
 
 CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED = range(6)
@@ -66,6 +67,11 @@ def load():
         "crv_last_error": (ctypes.c_char_p, []),
         "crv_status_string": (ctypes.c_char_p, [i]),
         "crv_launch_count": (ctypes.c_ulonglong, []),
+        "crv_profile_enable": (i, [u]),
+        "crv_profile_num_kinds": (i, []),
+        "crv_profile_kind_name": (ctypes.c_char_p, [i]),
+        "crv_profile_read": (i, [i, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(d)]),
+        "crv_profile_reset": (i, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(h, name)
@@ -120,6 +126,26 @@ def crv_status_string(s):
 
 def crv_launch_count():
     return int(load().crv_launch_count())
+
+
+def crv_profile_enable(kind_mask):
+    _check(load().crv_profile_enable(int(kind_mask)))
+
+
+def crv_profile_kinds():
+    h = load()
+    return [h.crv_profile_kind_name(k).decode() for k in range(h.crv_profile_num_kinds())]
+
+
+def crv_profile_read(k):
+    n = ctypes.c_ulonglong()
+    t = ctypes.c_double()
+    _check(load().crv_profile_read(int(k), ctypes.byref(n), ctypes.byref(t)))
+    return int(n.value), float(t.value)
+
+
+def crv_profile_reset():
+    _check(load().crv_profile_reset())
 
 
 def crv_plan_create(L, lam, J0, spin=0, nrule=CRV_NRULE_CURVELET, flags=0, max_batch=1, stream=None):

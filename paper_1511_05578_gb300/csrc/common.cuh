@@ -32,6 +32,23 @@ template <class T> __host__ __device__ __forceinline__ cx<T> mul_ipow(cx<T> a, i
 __host__ __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 __host__ __device__ __forceinline__ double parity_sign(int k) { return (k & 1) ? -1.0 : 1.0; }
 
+// Kernel kinds, for launch accounting and optional event timing.
+enum KernelKind {
+  K_DELTA = 0, K_SHT_CONTRACT, K_SHT_ROWS, K_BETA_SYNTH, K_BETA_QUAD, K_RING_INV_N, K_RING_INV_M,
+  K_RING_FWD_G, K_RING_FWD_A, K_CONTRACT_A, K_CONTRACT_S, K_TC_A, K_TC_S, K_MISC, K_NKINDS
+};
+const char* kind_name(int k);
+
+// Brackets one launch: records a start event on the stream if that kind is being
+// timed; done() records the end event and counts the launch.
+struct KTimer {
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  KTimer(int kind, cudaStream_t s);
+  void done();
+};
+
 // Record a launch of one of our kernels (host side).
 void count_launch();
 // Check the last launch; on failure store a message and return false.

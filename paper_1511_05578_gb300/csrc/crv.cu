@@ -21,6 +21,58 @@ static thread_local std::string g_err;
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- optional per-kind event timing -------------------------------------------
+static const char* kKindNames[K_NKINDS] = {"delta", "sht_contract", "sht_rows", "beta_synth", "beta_quad",
+                                           "ring_inv_n", "ring_inv_m", "ring_fwd_g", "ring_fwd_a",
+                                           "contract_analysis", "contract_synthesis", "tc_analysis",
+                                           "tc_synthesis", "misc"};
+const char* kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
+struct ProfState {
+  std::mutex mu;
+  std::atomic<unsigned> mask{0};
+  struct Pair { int kind; cudaEvent_t a, b; };
+  std::vector<Pair> pending;
+  std::vector<cudaEvent_t> free_events;
+  unsigned long long launches[K_NKINDS] = {0};
+  double ms[K_NKINDS] = {0};
+  cudaEvent_t get() {
+    if (!free_events.empty()) { cudaEvent_t e = free_events.back(); free_events.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain(size_t upto) {  // caller holds mu
+    for (size_t i = 0; i < upto && i < pending.size(); ++i) {
+      cudaEventSynchronize(pending[i].b);
+      float t = 0;
+      cudaEventElapsedTime(&t, pending[i].a, pending[i].b);
+      ms[pending[i].kind] += t;
+      free_events.push_back(pending[i].a);
+      free_events.push_back(pending[i].b);
+    }
+    pending.erase(pending.begin(), pending.begin() + std::min(upto, pending.size()));
+  }
+};
+static ProfState g_prof;
+
+KTimer::KTimer(int k, cudaStream_t st) : kind(k), s(st) {
+  if (!(g_prof.mask.load() & (1u << k))) return;
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  a = g_prof.get();
+  cudaEventRecord(a, s);
+}
+void KTimer::done() {
+  count_launch();
+  if (!a) return;
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  cudaEvent_t b = g_prof.get();
+  cudaEventRecord(b, s);
+  g_prof.pending.push_back({kind, a, b});
+  g_prof.launches[kind] += 1;
+  a = nullptr;
+  if (g_prof.pending.size() > 32768) g_prof.drain(16384);
+}
 bool launch_ok(const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -317,7 +369,7 @@ static bool set_smem(K kernel, size_t bytes) {
 }
 
 template <class T, bool COLFAST, class Ld, class St>
-static bool run_cols(const DftTab<T>& tb, int sign, int ncols, Ld ld, St st, cudaStream_t s) {
+static bool run_cols(int kind, const DftTab<T>& tb, int sign, int ncols, Ld ld, St st, cudaStream_t s) {
   if (ncols <= 0) return true;
   const size_t per = 2 * (size_t)tb.P * sizeof(cx<T>);
   int nb = (int)std::max<size_t>(1, std::min<size_t>(32, kSmemBudget / per));
@@ -328,9 +380,10 @@ static bool run_cols(const DftTab<T>& tb, int sign, int ncols, Ld ld, St st, cud
   if (!set_smem(kern, smem)) return false;
   int grid = (ncols + nb - 1) / nb;
   grid = std::min(grid, 152 * 16);
+  KTimer kt(kind, s);
   kern<<<grid, 256, smem, s>>>(tb, sign, ncols, nb, ld, st);
-  count_launch();
-  return launch_ok("dft_cols_kernel");
+  kt.done();
+  return launch_ok(kind_name(kind));
 }
 
 template <class T>
@@ -345,8 +398,9 @@ static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, 
   const size_t smem = per * nb;
   if (!set_smem(beta_quad_kernel<T>, smem)) return false;
   int grid = std::min((ncols + nb - 1) / nb, 152 * 16);
+  KTimer kt(K_BETA_QUAD, s);
   beta_quad_kernel<T><<<grid, 256, smem, s>>>(tb, ct, ncols, nb, Lb, Xb, Y, cs, scale, pa, pb, pc);
-  count_launch();
+  kt.done();
   return launch_ok("beta_quad_kernel");
 }
 
@@ -359,16 +413,20 @@ static bool sht_forward(crv_plan_s* p, const double* map, cx<double>* flm, int L
   const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
   LdMapRowT<double> ld{LdMapRow{map, N, real}};
   StSHTRow<double> sr{p->wF, Mc, m0, N, 1.0 / N};
-  if (!run_cols<double, false>(fs.d, -1, Ls, ld, sr, st)) return false;
+  if (!run_cols<double, false>(K_SHT_ROWS, fs.d, -1, Ls, ld, sr, st)) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
   if (!run_beta_quad<double>(fs, Ls, Mc, p->wF, p->wG, cs, 2 * M_PI, 1, 0, imod(3 * s, 4), st)) return false;
   cudaMemsetAsync(flm, 0, sizeof(cx<double>) * Ls * Ls, st);
   dim3 g((Mc + 127) / 128, Ls);
-  sht_fwd_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, p->wG, Ls, s, Mc, m0, flm);
-  count_launch();
+  {
+    KTimer kt(K_SHT_CONTRACT, st);
+    sht_fwd_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, p->wG, Ls, s, Mc, m0, flm);
+    kt.done();
+  }
   if (!launch_ok("sht_fwd_contract_kernel")) return false;
+  KTimer kt(K_MISC, st);
   flm_finish_kernel<<<(Ls * Ls + 255) / 256, 256, 0, st>>>(flm, Ls, s, real);
-  count_launch();
+  kt.done();
   return launch_ok("flm_finish_kernel");
 }
 
@@ -377,16 +435,17 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   const int N = 2 * Ls - 1;
   const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
   dim3 g((Mc + 127) / 128, Ls);
+  KTimer kt(K_SHT_CONTRACT, st);
   sht_inv_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, flm, Ls, s, Mc, m0, p->wG);
-  count_launch();
+  kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
   LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs};
   StRows<double> sr{p->wF, Mc, Ls};
-  if (!run_cols<double, true>(fs.d, +1, Mc, lb, sr, st)) return false;
+  if (!run_cols<double, true>(K_BETA_SYNTH, fs.d, +1, Mc, lb, sr, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
   StMapRow sm{map, N, real};
-  return run_cols<double, false>(fs.d, +1, Ls, lr, sm, st);
+  return run_cols<double, false>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -422,12 +481,14 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   }
   if (!used_tc) {
     dim3 g((cs.Nc + 63) / 64, (cs.Mc + 31) / 32, Lb);
+    KTimer kt(K_CONTRACT_A, st);
     contract_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, X);
-    count_launch();
+    kt.done();
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols<T, true>(dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs}, StRows<T>{Xb, ncols, Lb}, st))
+  if (!run_cols<T, true>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs},
+                         StRows<T>{Xb, ncols, Lb}, st))
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
@@ -435,10 +496,10 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     const int nr = std::min(Rr, Lb - b0);
     LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
     StContig<T> sc{R, N};
-    if (!run_cols<T, false>(dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
+    if (!run_cols<T, false>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
     LdRingM<T> lm{R, cs.Mc, cs.m0, N, p->real};
     StW<T, OutT> sw{W + (size_t)b0 * wstride, N, p->real};
-    if (!run_cols<T, true>(dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
+    if (!run_cols<T, true>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
   }
   return true;
 }
@@ -457,10 +518,10 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
     const int nr = std::min(Rr, Lb - b0);
     LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, p->real};
     StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
-    if (!run_cols<T, false>(dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
+    if (!run_cols<T, false>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
     LdRingA<T> la{R, cs.Nc, N};
     StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N};
-    if (!run_cols<T, true>(dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
+    if (!run_cols<T, true>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
@@ -469,8 +530,9 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   }
   const int mchunk = 16;
   dim3 g((Lb + 31) / 32, (cs.Mc + 31) / 32, (Lb + mchunk - 1) / mchunk);
+  KTimer kt(K_CONTRACT_S, st);
   contract_synthesis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, Y, psi_of<T>(p, j), Lb, cs, mchunk, flm);
-  count_launch();
+  kt.done();
   return launch_ok("contract_synthesis_kernel");
 }
 
@@ -485,8 +547,9 @@ static bool analysis_from_flm(crv_plan_s* p, const cx<double>* flm, void* const*
   }
   if (Wphi) {
     const int Lp = p->Lphi;
+    KTimer kt(K_MISC, st);
     scaling_apply_kernel<<<(Lp * Lp + 255) / 256, 256, 0, st>>>(p->dphi, Lp, flm, p->wflm2, false);
-    count_launch();
+    kt.done();
     if (!launch_ok("scaling_apply_kernel")) return false;
     const size_t pe = (size_t)Lp * (2 * Lp - 1) * (p->real ? 1 : 2);
     if (!sht_inverse(p, p->wflm2, Wphi + bidx * pe, Lp, 0, p->real, st)) return false;
@@ -508,12 +571,14 @@ static bool synthesis_to_flm(crv_plan_s* p, const void* const* W, size_t bidx, c
     const int Lp = p->Lphi;
     const size_t pe = (size_t)Lp * (2 * Lp - 1) * (p->real ? 1 : 2);
     if (!sht_forward(p, Wphi + bidx * pe, p->wflm2, Lp, 0, p->real, st)) return false;
+    KTimer kt(K_MISC, st);
     scaling_apply_kernel<<<(Lp * Lp + 255) / 256, 256, 0, st>>>(p->dphi, Lp, p->wflm2, flm, true);
-    count_launch();
+    kt.done();
     if (!launch_ok("scaling_apply_kernel")) return false;
   }
+  KTimer kt(K_MISC, st);
   flm_finish_kernel<<<(p->L * p->L + 255) / 256, 256, 0, st>>>(flm, p->L, p->spin, p->real);
-  count_launch();
+  kt.done();
   return launch_ok("flm_finish_kernel");
 }
 
@@ -552,6 +617,28 @@ const char* crv_status_string(int s) {
 }
 
 unsigned long long crv_launch_count(void) { return g_launches.load(); }
+
+int crv_profile_enable(unsigned kind_mask) {
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.mask.store(kind_mask);
+  return CRV_OK;
+}
+int crv_profile_num_kinds(void) { return K_NKINDS; }
+const char* crv_profile_kind_name(int k) { return kind_name(k); }
+int crv_profile_read(int k, unsigned long long* launches, double* total_ms) {
+  if (k < 0 || k >= K_NKINDS) return fail(CRV_EINVAL, "kind out of range");
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.drain(g_prof.pending.size());
+  if (launches) *launches = g_prof.launches[k];
+  if (total_ms) *total_ms = g_prof.ms[k];
+  return CRV_OK;
+}
+int crv_profile_reset(void) {
+  std::lock_guard<std::mutex> g(g_prof.mu);
+  g_prof.drain(g_prof.pending.size());
+  for (int k = 0; k < K_NKINDS; ++k) { g_prof.launches[k] = 0; g_prof.ms[k] = 0; }
+  return CRV_OK;
+}
 
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule, unsigned flags,
                     int max_batch, void* stream) {

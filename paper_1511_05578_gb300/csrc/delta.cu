@@ -89,8 +89,11 @@ cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_
     err = cudaMemsetAsync(q32, 0, n3 * sizeof(float), st);
     if (err != cudaSuccess) return err;
   }
-  delta_seed_kernel<<<(L + 127) / 128, 128, 0, st>>>(L, seed_v, seed_e);
-  count_launch();
+  {
+    KTimer kt(K_DELTA, st);
+    delta_seed_kernel<<<(L + 127) / 128, 128, 0, st>>>(L, seed_v, seed_e);
+    kt.done();
+  }
   if (!launch_ok("delta_seed_kernel")) return cudaErrorLaunchFailure;
   const size_t smem = sizeof(double) * 2 * (size_t)L;
   if (smem > 48 * 1024) {
@@ -98,8 +101,9 @@ cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_
     if (err != cudaSuccess) return err;
   }
   dim3 grid((L + 127) / 128, L);
+  KTimer kt(K_DELTA, st);
   delta_column_kernel<<<grid, 128, smem, st>>>(L, seed_v, seed_e, Q, q32);
-  count_launch();
+  kt.done();
   if (!launch_ok("delta_column_kernel")) return cudaErrorLaunchFailure;
   return cudaSuccess;
 }
