@@ -287,8 +287,8 @@ template <> const CorrTab<float>& corr_of<float>(const FftSet& s) { return s.cf;
 static int build_fft(crv_plan_s* p, int Lb) {
   if (p->fft.count(Lb)) return CRV_OK;
   const int N = 2 * Lb - 1;
-  const int P = next_pow2(2 * N - 1);
-  const int Q = next_pow2(4 * Lb - 3 > 1 ? 4 * Lb - 3 : 1);
+  const int P = std::max(8, next_pow2(2 * N - 1));
+  const int Q = std::max(8, next_pow2(4 * Lb - 3 > 1 ? 4 * Lb - 3 : 1));
   std::vector<std::complex<double>> tw(P), chirp(N), kf(P, 0.0), ki(P, 0.0), twq(Q), wv(Q, 0.0);
   for (int k = 0; k < P; ++k) tw[k] = std::polar(1.0, -2 * M_PI * (double)k / P);
   for (int t = 0; t < N; ++t) {
@@ -368,20 +368,41 @@ static bool set_smem(K kernel, size_t bytes) {
   return true;
 }
 
-template <class T, bool COLFAST, class Ld, class St>
+// Block shape of the FFT kernels: groups of P/8 threads, at least 256 threads.
+static int fft_threads(int P) { return std::max(P / 8, 256); }
+
+template <class T, class Ld, class St>
+static bool run_rows(int kind, const DftTab<T>& tb, int sign, int nrows, Ld ld, St st, cudaStream_t s) {
+  if (nrows <= 0) return true;
+  const int NT = fft_threads(tb.P), G = NT / (tb.P / 8);
+  const size_t smem = (size_t)G * padded_len(tb.P) * sizeof(cx<T>);
+  auto kern = rows_kernel<T, Ld, St>;
+  if (!set_smem(kern, smem)) return false;
+  const int per_sm = std::max(1, std::min(2048 / NT, (int)(200 * 1024 / std::max<size_t>(smem, 1))));
+  const int grid = std::max(1, std::min((nrows + G - 1) / G, 152 * per_sm * 2));
+  KTimer kt(kind, s);
+  kern<<<grid, NT, smem, s>>>(tb, sign, nrows, ld, st);
+  kt.done();
+  return launch_ok(kind_name(kind));
+}
+
+template <class T, class Ld, class St>
 static bool run_cols(int kind, const DftTab<T>& tb, int sign, int ncols, Ld ld, St st, cudaStream_t s) {
   if (ncols <= 0) return true;
-  const size_t per = 2 * (size_t)tb.P * sizeof(cx<T>);
-  int nb = (int)std::max<size_t>(1, std::min<size_t>(32, kSmemBudget / per));
-  const int maxnb = std::max(1, ncols / (2 * 152));
-  nb = std::min(nb, maxnb);
-  const size_t smem = per * nb;
-  auto kern = dft_cols_kernel<T, COLFAST, Ld, St>;
+  const int NT = fft_threads(tb.P), G = NT / (tb.P / 8);
+  const size_t work = (size_t)G * padded_len(tb.P) * sizeof(cx<T>);
+  const size_t colb = (size_t)(tb.N | 1) * sizeof(cx<T>);
+  // columns per group: a tile of about 64 KB, at most 8 per group
+  int cpg = (int)std::max<size_t>(1, std::min<size_t>(8, (64 * 1024) / (colb * G)));
+  cpg = std::min(cpg, std::max(1, ncols / (G * 152)));
+  const size_t smem = (size_t)G * cpg * colb + work;
+  auto kern = cols_kernel<T, Ld, St>;
   if (!set_smem(kern, smem)) return false;
-  int grid = (ncols + nb - 1) / nb;
-  grid = std::min(grid, 152 * 16);
+  const int Gc = G * cpg;
+  const int per_sm = std::max(1, std::min(2048 / NT, (int)(200 * 1024 / smem)));
+  const int grid = std::max(1, std::min((ncols + Gc - 1) / Gc, 152 * per_sm * 2));
   KTimer kt(kind, s);
-  kern<<<grid, 256, smem, s>>>(tb, sign, ncols, nb, ld, st);
+  kern<<<grid, NT, smem, s>>>(tb, sign, ncols, cpg, ld, st);
   kt.done();
   return launch_ok(kind_name(kind));
 }
@@ -391,15 +412,19 @@ static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, 
                           int pa, int pb, int pc, cudaStream_t s) {
   const DftTab<T>& tb = dft_of<T>(fs);
   const CorrTab<T>& ct = corr_of<T>(fs);
-  const int S = std::max(tb.P, ct.Q);
-  const size_t per = 2 * (size_t)S * sizeof(cx<T>);
-  int nb = (int)std::max<size_t>(1, std::min<size_t>(32, kSmemBudget / per));
-  nb = std::min(nb, std::max(1, ncols / (2 * 152)));
-  const size_t smem = per * nb;
+  if (ct.Q != tb.P) { g_err = "beta quadrature needs Q == P"; return false; }
+  const int NT = fft_threads(tb.P), G = NT / (tb.P / 8);
+  const size_t work = (size_t)G * padded_len(tb.P) * sizeof(cx<T>);
+  const size_t colb = (size_t)(Lb | 1) * sizeof(cx<T>);
+  int cpg = (int)std::max<size_t>(1, std::min<size_t>(8, (64 * 1024) / (colb * G)));
+  cpg = std::min(cpg, std::max(1, ncols / (G * 152)));
+  const size_t smem = (size_t)G * cpg * colb + work;
   if (!set_smem(beta_quad_kernel<T>, smem)) return false;
-  int grid = std::min((ncols + nb - 1) / nb, 152 * 16);
+  const int Gc = G * cpg;
+  const int per_sm = std::max(1, std::min(2048 / NT, (int)(200 * 1024 / smem)));
+  const int grid = std::max(1, std::min((ncols + Gc - 1) / Gc, 152 * per_sm * 2));
   KTimer kt(K_BETA_QUAD, s);
-  beta_quad_kernel<T><<<grid, 256, smem, s>>>(tb, ct, ncols, nb, Lb, Xb, Y, cs, scale, pa, pb, pc);
+  beta_quad_kernel<T><<<grid, NT, smem, s>>>(tb, ct, ncols, cpg, Lb, Xb, Y, cs, scale, pa, pb, pc);
   kt.done();
   return launch_ok("beta_quad_kernel");
 }
@@ -413,7 +438,7 @@ static bool sht_forward(crv_plan_s* p, const double* map, cx<double>* flm, int L
   const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
   LdMapRowT<double> ld{LdMapRow{map, N, real}};
   StSHTRow<double> sr{p->wF, Mc, m0, N, 1.0 / N};
-  if (!run_cols<double, false>(K_SHT_ROWS, fs.d, -1, Ls, ld, sr, st)) return false;
+  if (!run_rows<double>(K_SHT_ROWS, fs.d, -1, Ls, ld, sr, st)) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
   if (!run_beta_quad<double>(fs, Ls, Mc, p->wF, p->wG, cs, 2 * M_PI, 1, 0, imod(3 * s, 4), st)) return false;
   cudaMemsetAsync(flm, 0, sizeof(cx<double>) * Ls * Ls, st);
@@ -442,10 +467,10 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   ColSet cs{Mc, m0, 1, 0, 1, s};
   LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs};
   StRows<double> sr{p->wF, Mc, Ls};
-  if (!run_cols<double, true>(K_BETA_SYNTH, fs.d, +1, Mc, lb, sr, st)) return false;
+  if (!run_cols<double>(K_BETA_SYNTH, fs.d, +1, Mc, lb, sr, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
   StMapRow sm{map, N, real};
-  return run_cols<double, false>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
+  return run_rows<double>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -487,7 +512,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols<T, true>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs},
+  if (!run_cols<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs},
                          StRows<T>{Xb, ncols, Lb}, st))
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
@@ -496,10 +521,17 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     const int nr = std::min(Rr, Lb - b0);
     LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
     StContig<T> sc{R, N};
-    if (!run_cols<T, false>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
-    LdRingM<T> lm{R, cs.Mc, cs.m0, N, p->real};
-    StW<T, OutT> sw{W + (size_t)b0 * wstride, N, p->real};
-    if (!run_cols<T, true>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
+    if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
+    if (p->real) {  // Hermitian columns in pairs: real output in re and im
+      const int npair = (N + 1) / 2;
+      LdRingMPair<T> lm{R, cs.Mc, N, npair};
+      StWPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair};
+      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * npair, lm, sw, st)) return false;
+    } else {
+      LdRingM<T> lm{R, cs.Mc, cs.m0, N, false};
+      StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false};
+      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
+    }
   }
   return true;
 }
@@ -516,12 +548,19 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
-    LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, p->real};
-    StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
-    if (!run_cols<T, false>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
+    if (p->real) {  // real rows in pairs
+      const int nrows = nr * N;
+      LdWRowPair<T, InT> lw{W + (size_t)b0 * wstride, N, nrows};
+      StRingNPair<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, nrows, (T)1 / (T)N};
+      if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, (nrows + 1) / 2, lw, sn, st)) return false;
+    } else {
+      LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, false};
+      StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
+      if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
+    }
     LdRingA<T> la{R, cs.Nc, N};
     StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N};
-    if (!run_cols<T, true>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
+    if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
@@ -645,6 +684,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (!out) return fail(CRV_EINVAL, "out is NULL");
   *out = nullptr;
   if (L < 2 || L > 4096) return fail(CRV_EINVAL, "L must be in [2, 4096]");
+  if (L > 1024) return fail(CRV_EUNSUPPORTED, "this build's FFT engine supports L <= 1024 (P <= 4096)");
   if (!(lambda > 1.0) || !std::isfinite(lambda)) return fail(CRV_EINVAL, "lambda must be > 1");
   if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
   if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");

@@ -1,9 +1,15 @@
 // Shared-memory FFT engine for the odd lengths N = 2L_j - 1 of the MW / SO(3)
 // grids (Eqs. nodes_alpha..nodes_gamma). A length-N DFT is done by Bluestein's
 // chirp-z identity jk = (j^2 + k^2 - (k-j)^2)/2, which turns it into a cyclic
-// convolution of length P = 2^p >= 2N-1, itself done by a Stockham radix-4/2
-// power-of-two FFT in shared memory. One code path serves every length (the
-// prime factors of 2L-1 reach 89 at L = 1024).
+// convolution of length P = 2^p >= 2N-1, done by a register-blocked Stockham
+// power-of-two FFT (radix-8 passes, one radix-4 or radix-2 pass when p is not a
+// multiple of 3). One code path serves every length (the prime factors of 2L-1
+// reach 89 at L = 1024).
+//
+// A transform is run by a group of P/8 threads (one radix-8 butterfly each per
+// pass); several groups share a block and all groups advance in lockstep, so
+// block-wide barriers separate the passes. Shared-memory indices are padded by
+// one element every 32 to break the bank conflicts of the strided passes.
 #pragma once
 #include "common.cuh"
 
@@ -19,92 +25,6 @@ struct DftTab {
   const cx<T>* khat_i = nullptr;  // [P]  FFT_P(h wrapped) / P        (inverse DFT, sign +1)
 };
 
-// Stockham autosort FFT of `nb` independent length-P transforms held back to
-// back in x (each of length P); y is scratch of the same size. Returns the buffer
-// holding the result (x or y). dir = -1 forward (e^{-i}), +1 inverse (no 1/P).
-template <class T>
-__device__ cx<T>* fft_pow2(cx<T>* x, cx<T>* y, int P, int nb, const cx<T>* __restrict__ tw, int dir) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  int Ns = 1;
-  while (Ns < P) {
-    const int R = (P / Ns >= 4) ? 4 : 2;
-    const int nbf = P / R;             // butterflies per transform
-    const int stride = P / (Ns * R);   // twiddle index step
-    for (int t = tid; t < nb * nbf; t += nth) {
-      const int b = t / nbf, j = t - b * nbf;
-      const cx<T>* xb = x + (size_t)b * P;
-      cx<T>* yb = y + (size_t)b * P;
-      const int k = j & (Ns - 1);
-      const int out = ((j - k) * R) + k;
-      if (R == 4) {
-        cx<T> v0 = xb[j], v1 = xb[j + nbf], v2 = xb[j + 2 * nbf], v3 = xb[j + 3 * nbf];
-        if (Ns > 1) {
-          cx<T> w1 = tw[k * stride], w2 = tw[2 * k * stride], w3 = tw[3 * k * stride];
-          if (dir > 0) { w1 = conj(w1); w2 = conj(w2); w3 = conj(w3); }
-          v1 = v1 * w1; v2 = v2 * w2; v3 = v3 * w3;
-        }
-        cx<T> a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3, d = v1 - v3;
-        cx<T> a3 = (dir < 0) ? mk(d.im, -d.re) : mk(-d.im, d.re);
-        yb[out] = a0 + a2;
-        yb[out + Ns] = a1 + a3;
-        yb[out + 2 * Ns] = a0 - a2;
-        yb[out + 3 * Ns] = a1 - a3;
-      } else {
-        cx<T> v0 = xb[j], v1 = xb[j + nbf];
-        if (Ns > 1) {
-          cx<T> w1 = tw[k * stride];
-          if (dir > 0) w1 = conj(w1);
-          v1 = v1 * w1;
-        }
-        yb[out] = v0 + v1;
-        yb[out + Ns] = v0 - v1;
-      }
-    }
-    __syncthreads();
-    cx<T>* s = x; x = y; y = s;
-    Ns *= R;
-  }
-  return x;
-}
-
-// Bluestein DFT of `nb` length-N sequences. On entry buf[b*P + j], j < N, holds
-// x_j of sequence b (entries j >= N are ignored). On exit the returned pointer p
-// has X_k at p[b*P + k], k < N, where X_k = sum_j x_j e^{sign 2 pi i j k / N}.
-// buf and scr are shared-memory buffers of nb*P elements each.
-template <class T>
-__device__ cx<T>* dft_bluestein(cx<T>* buf, cx<T>* scr, int nb, const DftTab<T>& tb, int sign) {
-  const int tid = threadIdx.x, nth = blockDim.x;
-  const int N = tb.N, P = tb.P;
-  // a_j = x_j h^sign_j, zero padded
-  for (int t = tid; t < nb * P; t += nth) {
-    const int j = t % P;
-    cx<T> v = mk<T>(0, 0);
-    if (j < N) {
-      cx<T> h = tb.chirp[j];
-      if (sign > 0) h = conj(h);
-      v = buf[t] * h;
-    }
-    buf[t] = v;
-  }
-  __syncthreads();
-  cx<T>* r = fft_pow2(buf, scr, P, nb, tb.tw, -1);
-  cx<T>* o = (r == buf) ? scr : buf;
-  const cx<T>* kh = (sign < 0) ? tb.khat_f : tb.khat_i;
-  for (int t = tid; t < nb * P; t += nth) r[t] = r[t] * kh[t % P];
-  __syncthreads();
-  r = fft_pow2(r, o, P, nb, tb.tw, +1);
-  for (int t = tid; t < nb * P; t += nth) {
-    const int k = t % P;
-    if (k < N) {
-      cx<T> h = tb.chirp[k];
-      if (sign > 0) h = conj(h);
-      r[t] = r[t] * h;
-    }
-  }
-  __syncthreads();
-  return r;
-}
-
 // Power-of-two FFT tables of size Q (for the weight correlation of Eq. gmnmp).
 template <class T>
 struct CorrTab {
@@ -112,5 +32,138 @@ struct CorrTab {
   const cx<T>* tw = nullptr;    // [Q] e^{-2 pi i k/Q}
   const cx<T>* what = nullptr;  // [Q] FFT_Q(v)/Q, v[t] = w(-t), t in (-(2L-1), 2L-1) wrapped
 };
+
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
+__host__ __device__ __forceinline__ int padded_len(int P) { return P + (P >> 5) + 1; }
+
+template <class T>
+__device__ __forceinline__ cx<T> ld_tw(const cx<T>* __restrict__ tw, int idx, int dir) {
+  cx<T> w = tw[idx];
+  return dir > 0 ? conj(w) : w;
+}
+
+// In-register 8-point DFT (decimation in frequency), natural-order output.
+template <class T>
+__device__ __forceinline__ void dft8(cx<T>* v, int dir) {
+  const T s = (T)0.70710678118654752440;
+  cx<T> a0 = v[0] + v[4], b0 = v[0] - v[4];
+  cx<T> a1 = v[1] + v[5], b1 = v[1] - v[5];
+  cx<T> a2 = v[2] + v[6], b2 = v[2] - v[6];
+  cx<T> a3 = v[3] + v[7], b3 = v[3] - v[7];
+  if (dir < 0) {
+    b1 = mk((b1.re + b1.im) * s, (b1.im - b1.re) * s);   // * e^{-i pi/4}
+    b2 = mk(b2.im, -b2.re);                              // * -i
+    b3 = mk((b3.im - b3.re) * s, -(b3.re + b3.im) * s);  // * e^{-3i pi/4}
+  } else {
+    b1 = mk((b1.re - b1.im) * s, (b1.re + b1.im) * s);
+    b2 = mk(-b2.im, b2.re);
+    b3 = mk(-(b3.re + b3.im) * s, (b3.re - b3.im) * s);
+  }
+  cx<T> c0 = a0 + a2, c2 = a0 - a2, c1 = a1 + a3, d = a1 - a3;
+  cx<T> c3 = dir < 0 ? mk(d.im, -d.re) : mk(-d.im, d.re);
+  cx<T> e0 = b0 + b2, e2 = b0 - b2, e1 = b1 + b3, f = b1 - b3;
+  cx<T> e3 = dir < 0 ? mk(f.im, -f.re) : mk(-f.im, f.re);
+  v[0] = c0 + c1; v[4] = c0 - c1; v[2] = c2 + c3; v[6] = c2 - c3;
+  v[1] = e0 + e1; v[5] = e0 - e1; v[3] = e2 + e3; v[7] = e2 - e3;
+}
+
+// Power-of-two Stockham FFT of one length-P sequence held in x (padded indices), in
+// place, run by the Tt = P/8 threads of a group (lane tt). P >= 8. All groups of
+// the block must call this together (block barriers between passes).
+// dir = -1: X_k = sum x_j e^{-2 pi i jk/P}; dir = +1: e^{+...} (no 1/P).
+template <class T>
+__device__ void fft_p2(cx<T>* x, int P, const cx<T>* __restrict__ tw, int dir, int tt) {
+  const int Q8 = P >> 3;
+  int Ns = 1;
+  while (Ns < P) {
+    const int R = P / Ns;
+    if (R >= 8) {
+      const int j = tt, k = j & (Ns - 1);
+      cx<T> v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = x[padi(j + r * Q8)];
+      if (Ns > 1) {
+        const int st = P / (8 * Ns);
+        const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = ld_tw(tw, 2 * k * st, dir), w4 = ld_tw(tw, 4 * k * st, dir);
+        const cx<T> w3 = w1 * w2, w5 = w1 * w4, w6 = w2 * w4, w7 = w3 * w4;
+        v[1] = v[1] * w1; v[2] = v[2] * w2; v[3] = v[3] * w3; v[4] = v[4] * w4;
+        v[5] = v[5] * w5; v[6] = v[6] * w6; v[7] = v[7] * w7;
+      }
+      dft8(v, dir);
+      __syncthreads();
+      const int out = (j - k) * 8 + k;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[padi(out + r * Ns)] = v[r];
+      __syncthreads();
+      Ns *= 8;
+    } else if (R == 4) {
+      cx<T> v[2][4];
+      const int Q4 = P >> 2;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = tt + h * Q8, k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[h][r] = x[padi(j + r * Q4)];
+        if (Ns > 1) {
+          const int st = P / (4 * Ns);
+          const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = ld_tw(tw, 2 * k * st, dir), w3 = ld_tw(tw, 3 * k * st, dir);
+          v[h][1] = v[h][1] * w1; v[h][2] = v[h][2] * w2; v[h][3] = v[h][3] * w3;
+        }
+        cx<T> a0 = v[h][0] + v[h][2], a1 = v[h][0] - v[h][2], a2 = v[h][1] + v[h][3], d = v[h][1] - v[h][3];
+        cx<T> a3 = dir < 0 ? mk(d.im, -d.re) : mk(-d.im, d.re);
+        v[h][0] = a0 + a2; v[h][1] = a1 + a3; v[h][2] = a0 - a2; v[h][3] = a1 - a3;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = tt + h * Q8, k = j & (Ns - 1), out = (j - k) * 4 + k;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[padi(out + r * Ns)] = v[h][r];
+      }
+      __syncthreads();
+      Ns *= 4;
+    } else {  // R == 2
+      cx<T> v[4][2];
+      const int Q2 = P >> 1;
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int j = tt + h * Q8, k = j & (Ns - 1);
+        v[h][0] = x[padi(j)];
+        v[h][1] = x[padi(j + Q2)];
+        if (Ns > 1) v[h][1] = v[h][1] * ld_tw(tw, k * (P / (2 * Ns)), dir);
+        cx<T> a = v[h][0] + v[h][1], b = v[h][0] - v[h][1];
+        v[h][0] = a; v[h][1] = b;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int j = tt + h * Q8, k = j & (Ns - 1), out = (j - k) * 2 + k;
+        x[padi(out)] = v[h][0];
+        x[padi(out + Ns)] = v[h][1];
+      }
+      __syncthreads();
+      Ns *= 2;
+    }
+  }
+}
+
+// Bluestein core on one sequence: on entry x[padi(j)] holds x_j h^sign_j for j < N
+// and 0 for N <= j < P; on exit x[padi(k)] holds the cyclic convolution with the
+// chirp kernel, so X_k = h^sign_k * x[padi(k)], k < N. Group-cooperative.
+template <class T>
+__device__ void bluestein_conv(cx<T>* x, const DftTab<T>& tb, int sign, int tt) {
+  const int P = tb.P, Tt = P >> 3;
+  fft_p2(x, P, tb.tw, -1, tt);
+  const cx<T>* kh = (sign < 0) ? tb.khat_f : tb.khat_i;
+  for (int i = tt; i < P; i += Tt) x[padi(i)] = x[padi(i)] * kh[i];
+  __syncthreads();
+  fft_p2(x, P, tb.tw, +1, tt);
+}
+
+template <class T>
+__device__ __forceinline__ cx<T> chirp_of(const DftTab<T>& tb, int j, int sign) {
+  cx<T> h = tb.chirp[j];
+  return sign > 0 ? conj(h) : h;
+}
 
 }  // namespace crv
