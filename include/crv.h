@@ -153,6 +153,27 @@ const char* crv_status_string(int status);
  * threads). Used to count device work inside timed regions. */
 unsigned long long crv_launch_count(void);
 
+/* Allocation-free build of the Delta^l = d^l(pi/2) quarter table. The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device
+ * memory themselves, such as code that runs inside a host framework owning a fixed
+ * device arena, code issued while a stream is being captured into a CUDA graph, or
+ * latency-critical paths where the implicit synchronisation of cudaMalloc/cudaFree
+ * is not acceptable. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   L       1 <= L <= CRV_NOALLOC_MAX_L
+ *   Q       caller-owned device buffer of L*L*L doubles; on return (stream order) it holds
+ *           Q[m'][l][n] = Delta^l_{m'n} for 0 <= m', n <= l < L and 0 elsewhere, the same
+ *           values crv_plan_delta reads back from a plan of band limit >= L
+ *   stream  CUDA stream (NULL = legacy default stream)
+ * Scratch: the recursion's per-l seed rows live in a library-wide device array sized for
+ * CRV_NOALLOC_MAX_L (3 MB); every GPU that loads libcrv holds it until the process exits.
+ * The first call on a device looks up that array's device address with the device
+ * current; make that first call before any stream capture. All calls share the array,
+ * so calls that overlap on the GPU (different streams, or devices sharing a context)
+ * race; serialise them. Errors: CRV_EINVAL for L outside the range or Q == NULL,
+ * CRV_ECUDA for a failed address lookup or launch (message in crv_last_error()). */
+#define CRV_NOALLOC_MAX_L 512
+int crv_delta_table_noalloc(int L, double* Q, void* stream);
+
 /* Optional per-kernel timing for measurement tools. When bit k of kind_mask is set,
  * every launch of kernel kind k is bracketed by CUDA events recorded on the stream it
  * is launched on; crv_profile_read waits for the recorded events and returns the

@@ -17,7 +17,7 @@ __all__ = [
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CrvError",
     "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
-    "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_last_error", "crv_status_string",
+    "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
     "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
     "Plan",
 ]
@@ -67,6 +67,7 @@ def load():
         "crv_last_error": (ctypes.c_char_p, []),
         "crv_status_string": (ctypes.c_char_p, [i]),
         "crv_launch_count": (ctypes.c_ulonglong, []),
+        "crv_delta_table_noalloc": (i, [i, vp, vp]),
         "crv_profile_enable": (i, [u]),
         "crv_profile_num_kinds": (i, []),
         "crv_profile_kind_name": (ctypes.c_char_p, [i]),
@@ -187,6 +188,15 @@ def crv_plan_scaling(plan, out):
 def crv_plan_delta(plan, l, out):
     _check(load().crv_plan_delta(plan, int(l), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+CRV_NOALLOC_MAX_L = 512
+
+
+def crv_delta_table_noalloc(L, Q, stream=None):
+    """Delta quarter table [L][L][L] (float64 device tensor Q) built without any device
+    allocation by the library: for callers that must not allocate (see include/crv.h)."""
+    _check(load().crv_delta_table_noalloc(int(L), _ptr(Q), _stream(stream)))
 
 
 def crv_sht_fwd(plan, fmap, flm, B, stream=None):

@@ -82,6 +82,7 @@ bool launch_ok(const char* what) {
   return true;
 }
 static int fail(int code, const std::string& msg) { g_err = msg; return code; }
+void set_error(const std::string& msg) { g_err = msg; }
 
 cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_e, cudaStream_t st);
 // tensor-core contractions (tc_contract.cu)

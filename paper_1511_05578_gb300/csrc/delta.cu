@@ -108,4 +108,76 @@ cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free build of the Delta table for callers that cannot allocate
+// device memory (see crv_delta_table_noalloc in include/crv.h). The seed row
+// scratch lives in file-scope device arrays sized for L <= CRV_NOALLOC_MAX_L;
+// every GPU that loads the library holds them (3 MB) until the process exits.
+// ---------------------------------------------------------------------------
+constexpr int kNoallocMaxL = 512;
+static __device__ __align__(256) double g_noalloc_seed_v[kNoallocMaxL * kNoallocMaxL];
+static __device__ __align__(256) int g_noalloc_seed_e[kNoallocMaxL * kNoallocMaxL];
+
 }  // namespace crv
+
+#include <mutex>
+#include <string>
+#include "../../include/crv.h"
+
+namespace crv {
+void set_error(const std::string& msg);  // crv.cu: message returned by crv_last_error()
+}
+
+namespace {
+// Device addresses of the scratch arrays, looked up once per device. Host code must
+// not hand the symbols themselves to a kernel: on the host they are stand-ins, not
+// device addresses.
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_v[kMaxDevices] = {nullptr};
+int* g_noalloc_e[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int crv_delta_table_noalloc(int L, double* Q, void* stream) {
+  if (L < 1 || L > crv::kNoallocMaxL) {
+    crv::set_error("crv_delta_table_noalloc: L must be in [1, " + std::to_string(crv::kNoallocMaxL) + "]");
+    return CRV_EINVAL;
+  }
+  if (!Q) { crv::set_error("crv_delta_table_noalloc: Q is NULL"); return CRV_EINVAL; }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    crv::set_error("crv_delta_table_noalloc: no usable current device");
+    return CRV_ECUDA;
+  }
+  double* sv;
+  int* se;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_v[dev]) {
+      void* pv = nullptr;
+      void* pe = nullptr;
+      cudaError_t e1 = cudaGetSymbolAddress(&pv, crv::g_noalloc_seed_v);
+      cudaError_t e2 = (e1 == cudaSuccess) ? cudaGetSymbolAddress(&pe, crv::g_noalloc_seed_e) : e1;
+      if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        crv::set_error(std::string("crv_delta_table_noalloc: cudaGetSymbolAddress failed: ") +
+                       cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+        return CRV_ECUDA;
+      }
+      g_noalloc_v[dev] = (double*)pv;
+      g_noalloc_e[dev] = (int*)pe;
+    }
+    sv = g_noalloc_v[dev];
+    se = g_noalloc_e[dev];
+  }
+  // the seed kernel writes every entry the column kernel reads (n <= l < L), so the
+  // scratch needs no clearing; the output table is cleared by build_delta.
+  cudaError_t e = crv::build_delta(L, Q, nullptr, sv, se, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    crv::set_error(std::string("crv_delta_table_noalloc: ") + cudaGetErrorString(e));
+    return CRV_ECUDA;
+  }
+  return CRV_OK;
+}
+
