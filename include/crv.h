@@ -102,6 +102,11 @@ int crv_plan_destroy(crv_plan_t plan);
 int crv_plan_info(crv_plan_t plan, int* J, int* Lj, size_t* w_elems, int* L_phi,
                   size_t* workspace_bytes);
 
+/* Wait for the device and report whether any bounded device-side wait of this plan's
+ * kernels gave up since the last check (CRV_ETIMEOUT; the affected results are
+ * invalid). Clears the condition. */
+int crv_plan_check(crv_plan_t plan);
+
 /* Host copy of plan tables, for inspection and tests.
  *   crv_plan_kernel:  psi[l][n + L_j - 1] = sPsi^(j)_ln (real, Eq. wav_factorized), l < L_j
  *   crv_plan_scaling: phi[l] = sqrt(4pi/(2l+1)) Phi_l0 = sqrt(k_lambda(l/lambda^J0)), l < L

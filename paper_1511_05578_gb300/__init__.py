@@ -15,7 +15,7 @@ import os
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CrvError",
-    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_kernel",
+    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_check", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
     "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
     "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
@@ -55,6 +55,7 @@ def load():
         "crv_plan_destroy": (i, [vp]),
         "crv_plan_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i),
                               ctypes.POINTER(sz)]),
+        "crv_plan_check": (i, [vp]),
         "crv_plan_kernel": (i, [vp, i, ctypes.POINTER(d)]),
         "crv_plan_scaling": (i, [vp, ctypes.POINTER(d)]),
         "crv_plan_delta": (i, [vp, i, ctypes.POINTER(d)]),
@@ -172,6 +173,11 @@ def crv_plan_info(plan):
     ws = ctypes.c_size_t()
     _check(h.crv_plan_info(plan, ctypes.byref(J), Lj, we, ctypes.byref(Lp), ctypes.byref(ws)))
     return {"J": J.value, "Lj": list(Lj), "w_elems": list(we), "L_phi": Lp.value, "workspace_bytes": ws.value}
+
+
+def crv_plan_check(plan):
+    """Synchronise and raise CrvError(CRV_ETIMEOUT) if a bounded device wait gave up."""
+    _check(load().crv_plan_check(plan))
 
 
 def crv_plan_kernel(plan, j, out):

@@ -30,6 +30,18 @@ template <class T> __host__ __device__ __forceinline__ cx<T> mul_ipow(cx<T> a, i
   }
 }
 __host__ __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+// Exact division of 32-bit unsigned n by a runtime constant d (1 <= d < 2^32) with a
+// 64-bit reciprocal M = floor((2^64-1)/d) + 1: n / d = mulhi64(M, n) (Lemire et al.,
+// "Faster remainder by direct computation", 2019).
+struct FastDiv {
+  uint32_t d = 1;
+  uint64_t M = 0;
+  FastDiv() = default;
+  __host__ explicit FastDiv(uint32_t dd) : d(dd), M(~0ull / dd + 1) {}
+  __device__ __forceinline__ uint32_t div(uint32_t n) const { return d == 1 ? n : (uint32_t)__umul64hi(M, (uint64_t)n); }
+  __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
 __host__ __device__ __forceinline__ double parity_sign(int k) { return (k & 1) ? -1.0 : 1.0; }
 
 // Kernel kinds, for launch accounting and optional event timing.

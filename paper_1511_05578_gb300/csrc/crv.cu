@@ -4,6 +4,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -86,11 +87,10 @@ void set_error(const std::string& msg) { g_err = msg; }
 
 cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_e, cudaStream_t st);
 // tensor-core contractions (tc_contract.cu)
-bool tc_analysis(const float* Q32, int Lmax, const cx<double>* flm, const float* psi, int Lb, ColSet cs,
-                 cx<float>* X, void* scratch, size_t scratch_bytes, cudaStream_t st);
-bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, const float* psi, int Lb, ColSet cs,
-                  cx<double>* flm, void* scratch, size_t scratch_bytes, cudaStream_t st);
-size_t tc_scratch_bytes(int Lmax, int Mc, int Nc);
+bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, const float* psi, int Lb, ColSet cs,
+                 cx<float>* X, int* err, cudaStream_t st);
+bool tc_synthesis(const float* Q32, const double* Q64, int Lmax, const cx<float>* Y, const float* psi, int Lb,
+                  ColSet cs, cx<float>* Zscratch, cx<double>* flm, int* err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Host numerics for the plan tables
@@ -236,13 +236,14 @@ struct crv_plan_s {
   // workspace
   cx<double>* wflm = nullptr;
   cx<double>* wflm2 = nullptr;
+  cx<float>* wflm32 = nullptr;  // FP32 copy of the analysed f_lm (tensor-core operand source)
   cx<double>* wF = nullptr;
   cx<double>* wG = nullptr;
   void* wX = nullptr;
   void* wXb = nullptr;
   void* wR = nullptr;
-  void* wTC = nullptr;
-  size_t tc_bytes = 0;
+  bool use_tc = false;   // tensor-core contractions (mixed plans)
+  int* d_err = nullptr;   // set by kernels whose bounded waits gave up
   size_t vol_bytes = 0, ring_bytes = 0;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -275,7 +276,11 @@ struct crv_plan_s {
     return n;
   }
   int nc(int Lb) const { return (-n0(Lb) - n0(Lb)) / nstep() + 1; }
-  ColSet colset(int Lb) const { ColSet c; c.Mc = mc(Lb); c.m0 = m0(Lb); c.Nc = nc(Lb); c.n0 = n0(Lb); c.nstep = nstep(); c.extra = 0; return c; }
+  ColSet colset(int Lb) const {
+    ColSet c; c.Mc = mc(Lb); c.m0 = m0(Lb); c.Nc = nc(Lb); c.n0 = n0(Lb); c.nstep = nstep(); c.extra = 0;
+    c.fNc = FastDiv((uint32_t)c.Nc);
+    return c;
+  }
 };
 
 template <class T> static const DftTab<T>& dft_of(const FftSet& s);
@@ -290,7 +295,11 @@ static int build_fft(crv_plan_s* p, int Lb) {
   const int N = 2 * Lb - 1;
   const int P = std::max(8, next_pow2(2 * N - 1));
   const int Q = std::max(8, next_pow2(4 * Lb - 3 > 1 ? 4 * Lb - 3 : 1));
-  std::vector<std::complex<double>> tw(P), chirp(N), kf(P, 0.0), ki(P, 0.0), twq(Q), wv(Q, 0.0);
+  std::vector<std::complex<double>> tw(P), chirp(N), kf(P, 0.0), ki(P, 0.0), twq(Q), wv(Q, 0.0), hp(N);
+  for (int j = 0; j < N; ++j) {  // e^{i pi m/N} with m = j or j - N (|m| < Lb)
+    const int m = (j < Lb) ? j : j - N;
+    hp[j] = std::polar(1.0, M_PI * (double)m / N);
+  }
   for (int k = 0; k < P; ++k) tw[k] = std::polar(1.0, -2 * M_PI * (double)k / P);
   for (int t = 0; t < N; ++t) {
     long long r = ((long long)t * t) % (2LL * N);
@@ -340,6 +349,7 @@ static int build_fft(crv_plan_s* p, int Lb) {
   up(chirp, d, f); s.d.chirp = d; s.f.chirp = f;
   up(kf, d, f); s.d.khat_f = d; s.f.khat_f = f;
   up(ki, d, f); s.d.khat_i = d; s.f.khat_i = f;
+  up(hp, d, f); s.d.hphase = d; s.f.hphase = f;
   s.cd.Q = s.cf.Q = Q;
   up(twq, d, f); s.cd.tw = d; s.cf.tw = f;
   up(wv, d, f); s.cd.what = d; s.cf.what = f;
@@ -351,7 +361,6 @@ static int build_fft(crv_plan_s* p, int Lb) {
 // ---------------------------------------------------------------------------
 // Launch helpers
 // ---------------------------------------------------------------------------
-static const size_t kSmemBudget = 200 * 1024;
 
 template <class K>
 static bool set_smem(K kernel, size_t bytes) {
@@ -403,7 +412,7 @@ static bool run_cols(int kind, const DftTab<T>& tb, int sign, int ncols, Ld ld, 
   const int per_sm = std::max(1, std::min(2048 / NT, (int)(200 * 1024 / smem)));
   const int grid = std::max(1, std::min((ncols + Gc - 1) / Gc, 152 * per_sm * 2));
   KTimer kt(kind, s);
-  kern<<<grid, NT, smem, s>>>(tb, sign, ncols, cpg, ld, st);
+  kern<<<grid, NT, smem, s>>>(tb, sign, ncols, cpg, FastDiv((uint32_t)Gc), ld, st);
   kt.done();
   return launch_ok(kind_name(kind));
 }
@@ -425,7 +434,8 @@ static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, 
   const int per_sm = std::max(1, std::min(2048 / NT, (int)(200 * 1024 / smem)));
   const int grid = std::max(1, std::min((ncols + Gc - 1) / Gc, 152 * per_sm * 2));
   KTimer kt(K_BETA_QUAD, s);
-  beta_quad_kernel<T><<<grid, NT, smem, s>>>(tb, ct, ncols, cpg, Lb, Xb, Y, cs, scale, pa, pb, pc);
+  beta_quad_kernel<T><<<grid, NT, smem, s>>>(tb, ct, ncols, cpg, Lb, FastDiv((uint32_t)Gc), Xb, Y, cs, scale, pa,
+                                             pb, pc);
   kt.done();
   return launch_ok("beta_quad_kernel");
 }
@@ -466,7 +476,7 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
-  LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs};
+  LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs, fs.d.hphase};
   StRows<double> sr{p->wF, Mc, Ls};
   if (!run_cols<double>(K_BETA_SYNTH, fs.d, +1, Mc, lb, sr, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
@@ -500,8 +510,8 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   cx<T>* R = (cx<T>*)p->wR;
   bool used_tc = false;
   if constexpr (sizeof(T) == 4) {
-    if (p->wTC) {
-      if (!tc_analysis(p->dQ32, p->L, flm, p->dpsi32[j], Lb, cs, (cx<float>*)X, p->wTC, p->tc_bytes, st)) return false;
+    if (p->use_tc) {
+      if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->dpsi32[j], Lb, cs, (cx<float>*)X, p->d_err, st)) return false;
       used_tc = true;
     }
   }
@@ -513,7 +523,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs},
+  if (!run_cols<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase},
                          StRows<T>{Xb, ncols, Lb}, st))
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
@@ -525,12 +535,12 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
     if (p->real) {  // Hermitian columns in pairs: real output in re and im
       const int npair = (N + 1) / 2;
-      LdRingMPair<T> lm{R, cs.Mc, N, npair};
-      StWPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair};
+      LdRingMPair<T> lm{R, cs.Mc, N, npair, FastDiv((uint32_t)npair)};
+      StWPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
       if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * npair, lm, sw, st)) return false;
     } else {
-      LdRingM<T> lm{R, cs.Mc, cs.m0, N, false};
-      StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false};
+      LdRingM<T> lm{R, cs.Mc, cs.m0, N, false, FastDiv((uint32_t)N)};
+      StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false, FastDiv((uint32_t)N)};
       if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
     }
   }
@@ -559,14 +569,17 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
       StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
     }
-    LdRingA<T> la{R, cs.Nc, N};
-    StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N};
+    LdRingA<T> la{R, cs.Nc, N, FastDiv((uint32_t)cs.Nc)};
+    StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N, FastDiv((uint32_t)cs.Nc)};
     if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
   if constexpr (sizeof(T) == 4) {
-    if (p->wTC) return tc_synthesis(p->dQ32, p->L, Y, p->dpsi32[j], Lb, cs, flm, p->wTC, p->tc_bytes, st);
+    // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
+    if (p->use_tc)
+      return tc_synthesis(p->dQ32, p->dQ, p->L, (const cx<float>*)Y, p->dpsi32[j], Lb, cs, (cx<float>*)p->wXb, flm,
+                          p->d_err, st);
   }
   const int mchunk = 16;
   dim3 g((Lb + 31) / 32, (cs.Mc + 31) / 32, (Lb + mchunk - 1) / mchunk);
@@ -579,6 +592,13 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
 template <class T, class WT>
 static bool analysis_from_flm(crv_plan_s* p, const cx<double>* flm, void* const* W, size_t bidx, double* Wphi,
                               cudaStream_t st) {
+  if (p->use_tc) {
+    const int n = p->L * p->L;
+    KTimer kt(K_MISC, st);
+    cast_flm_kernel<float><<<(n + 255) / 256, 256, 0, st>>>(flm, p->wflm32, n);
+    kt.done();
+    if (!launch_ok("cast_flm_kernel")) return false;
+  }
   for (int j = p->J0; j <= p->J; ++j) {
     const int Lb = p->Lj[j], N = 2 * Lb - 1;
     const size_t we = (size_t)Lb * N * N * (p->real ? 1 : 2);
@@ -773,19 +793,23 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->vol_bytes = (size_t)L * Mc * Nc * el;
   p->wflm = p->dalloc<cx<double>>((size_t)L * L, &stt);
   p->wflm2 = p->dalloc<cx<double>>((size_t)L * L, &stt);
+  p->wflm32 = p->dalloc<cx<float>>((size_t)L * L, &stt);
   p->wF = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
   p->wG = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
   p->wX = p->dalloc<unsigned char>(p->vol_bytes, &stt);
-  p->wXb = p->dalloc<unsigned char>(p->vol_bytes, &stt);
+  // Xb; in the mixed path it also holds the synthesis products Z[m'][mi][l] (L x Mc x L)
+  p->wXb = p->dalloc<unsigned char>(std::max(p->vol_bytes, (size_t)L * Mc * L * el), &stt);
+  p->d_err = p->dalloc<int>(1, &stt);
+  if (stt == CRV_OK) cudaMemset(p->d_err, 0, sizeof(int));
   {
     // ring-chunk buffer: at least one ring, at most all rings, about 96 MB (L2-resident)
     const size_t one = (size_t)N * std::max(Mc, Nc) * el;
     p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)96 << 20));
   }
   p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
-  if (p->mixed && stt == CRV_OK) {
-    p->tc_bytes = tc_scratch_bytes(L, Mc, Nc);
-    if (p->tc_bytes) p->wTC = p->dalloc<unsigned char>(p->tc_bytes, &stt);
+  {
+    const char* e = getenv("CRV_DISABLE_TC");
+    p->use_tc = p->mixed && !(e && e[0] && e[0] != '0');
   }
   if (stt != CRV_OK) { delete p; return stt; }
   // Delta tables
@@ -828,6 +852,19 @@ int crv_plan_info(crv_plan_t p, int* J, int* Lj, size_t* w_elems, int* L_phi, si
   }
   if (L_phi) *L_phi = p->Lphi;
   if (workspace_bytes) *workspace_bytes = p->bytes;
+  return CRV_OK;
+}
+
+int crv_plan_check(crv_plan_t p) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
+  int h = 0;
+  cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (h) {
+    cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
+  }
   return CRV_OK;
 }
 

@@ -23,6 +23,7 @@ struct DftTab {
   const cx<T>* chirp = nullptr;   // [N]  h_t = e^{-i pi t^2 / N}
   const cx<T>* khat_f = nullptr;  // [P]  FFT_P(conj h wrapped) / P   (forward DFT, sign -1)
   const cx<T>* khat_i = nullptr;  // [P]  FFT_P(h wrapped) / P        (inverse DFT, sign +1)
+  const cx<T>* hphase = nullptr;  // [N]  e^{+i pi m/N}, m = j (j < (N+1)/2) or j - N: half-sample phase of beta_b
 };
 
 // Power-of-two FFT tables of size Q (for the weight correlation of Eq. gmnmp).
@@ -84,7 +85,7 @@ __device__ void fft_p2(cx<T>* x, int P, const cx<T>* __restrict__ tw, int dir, i
       for (int r = 0; r < 8; ++r) v[r] = x[padi(j + r * Q8)];
       if (Ns > 1) {
         const int st = P / (8 * Ns);
-        const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = ld_tw(tw, 2 * k * st, dir), w4 = ld_tw(tw, 4 * k * st, dir);
+        const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = w1 * w1, w4 = w2 * w2;
         const cx<T> w3 = w1 * w2, w5 = w1 * w4, w6 = w2 * w4, w7 = w3 * w4;
         v[1] = v[1] * w1; v[2] = v[2] * w2; v[3] = v[3] * w3; v[4] = v[4] * w4;
         v[5] = v[5] * w5; v[6] = v[6] * w6; v[7] = v[7] * w7;

@@ -13,9 +13,16 @@ namespace crv {
 
 struct ColSet {
   int Mc, m0, Nc, n0, nstep;
-  int extra;  // added to m+n in parities and phases (spin for the SHT)
-  __device__ __forceinline__ int m_of(int c) const { return m0 + c / Nc; }
-  __device__ __forceinline__ int n_of(int c) const { return n0 + nstep * (c % Nc); }
+  int extra;    // added to m+n in parities and phases (spin for the SHT)
+  FastDiv fNc;  // division by Nc
+  __device__ __forceinline__ int m_of(int c) const { return m0 + (int)fNc.div((uint32_t)c); }
+  __device__ __forceinline__ int n_of(int c) const { return n0 + nstep * (int)fNc.mod((uint32_t)c); }
+  // parity of m + n + extra for column c
+  __device__ __forceinline__ int par(int c) const {
+    const uint32_t q = fNc.div((uint32_t)c);
+    const int m = m0 + (int)q, n = n0 + nstep * (int)((uint32_t)c - q * (uint32_t)Nc);
+    return (m + n + extra) & 1;
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -57,7 +64,8 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) rows_kernel(DftTa
 }
 
 template <class T, class Ld, class St>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTab<T> tb, int sign, int ncols, int cpg, Ld ld, St st) {
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTab<T> tb, int sign, int ncols, int cpg,
+                                                                          FastDiv fgc, Ld ld, St st) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, P = tb.P, Tt = P >> 3, PL = padded_len(P);
   const int G = blockDim.x / Tt, g = threadIdx.x / Tt, tt = threadIdx.x % Tt;
@@ -67,7 +75,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTa
   cx<T>* buf = tile + (size_t)Gc * CS + (size_t)g * PL;    // per group work buffer
   for (int c0 = blockIdx.x * Gc; c0 < ncols; c0 += gridDim.x * Gc) {
     for (int t = threadIdx.x; t < Gc * N; t += blockDim.x) {
-      const int b = t % Gc, j = t / Gc, c = c0 + b;
+      const int j = (int)fgc.div(t), b = t - j * Gc, c = c0 + b;
       tile[(size_t)b * CS + j] = (c < ncols) ? ld(c, j) : mk<T>(0, 0);
     }
     __syncthreads();
@@ -81,7 +89,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTa
       __syncthreads();
     }
     for (int t = threadIdx.x; t < Gc * N; t += blockDim.x) {
-      const int b = t % Gc, k = t / Gc, c = c0 + b;
+      const int k = (int)fgc.div(t), b = t - k * Gc, c = c0 + b;
       if (c < ncols) {
         const int kn = (k == 0) ? 0 : N - k;
         st(c, k, tile[(size_t)b * CS + k], tile[(size_t)b * CS + kn]);
@@ -99,16 +107,13 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTa
 // z_{m' mod N} = X~_{m'} e^{i m' pi/N}, X~_{-m'} = (-1)^{m+n+extra} X~_{m'}.
 template <class T>
 struct LdBetaSynth {
-  const cx<T>* X; int C, K, N; ColSet cs;
+  const cx<T>* X; int C, K, N; ColSet cs; const cx<T>* hphase;
   __device__ cx<T> operator()(int c, int j) const {
     int mp = (j < K) ? j : j - N;
     int a = mp < 0 ? -mp : mp;
     cx<T> v = X[(size_t)a * C + c];
-    if (mp < 0 && ((cs.m_of(c) + cs.n_of(c) + cs.extra) & 1)) v = mk(-v.re, -v.im);
-    T s, co;
-    if (sizeof(T) == 8) { double sd, cd; sincospi((double)mp / (double)N, &sd, &cd); s = (T)sd; co = (T)cd; }
-    else { float sf, cf; sincospif((float)mp / (float)N, &sf, &cf); s = (T)sf; co = (T)cf; }
-    return v * mk(co, s);
+    if (mp < 0 && cs.par(c)) v = mk(-v.re, -v.im);
+    return v * hphase[j];
   }
 };
 // keep k < Kout, Y[k][c]
@@ -142,9 +147,9 @@ struct StContig {  // out[c][k], k < N
 // real: Hermitian completion z_{N-m} = conj(z_m), output real part.
 template <class T>
 struct LdRingM {
-  const cx<T>* Tb; int Mc, m0, N; bool real;
+  const cx<T>* Tb; int Mc, m0, N; bool real; FastDiv fN;
   __device__ cx<T> operator()(int c, int j) const {
-    const int b = c / N, g = c % N;
+    const int b = (int)fN.div(c), g = c - b * N;
     const cx<T>* base = Tb + (size_t)b * Mc * N + g;
     int m = (j <= (N - 1) / 2) ? j : j - N;
     if (real) {
@@ -158,9 +163,9 @@ struct LdRingM {
 };
 template <class T, class OutT>
 struct StW {  // W[b][a][g] in OutT, real or complex
-  OutT* W; int N; bool real;
+  OutT* W; int N; bool real; FastDiv fN;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
-    const int b = c / N, g = c % N;
+    const int b = (int)fN.div(c), g = c - b * N;
     const size_t idx = ((size_t)b * N + k) * N + g;
     if (real) W[idx] = (OutT)v.re;
     else { W[2 * idx] = (OutT)v.re; W[2 * idx + 1] = (OutT)v.im; }
@@ -191,17 +196,17 @@ struct StRingN {  // U[c][ni] = D[n mod N] / N for n in the n-set
 // Ring forward, step over a: column (b, ni) of U[b][a][ni] -> Xb[b][mi][ni].
 template <class T>
 struct LdRingA {
-  const cx<T>* U; int Nc, N;
+  const cx<T>* U; int Nc, N; FastDiv fNc;
   __device__ cx<T> operator()(int c, int j) const {
-    const int b = c / Nc, ni = c % Nc;
+    const int b = (int)fNc.div(c), ni = c - b * Nc;
     return U[((size_t)b * N + j) * Nc + ni];
   }
 };
 template <class T>
 struct StRingA {
-  cx<T>* Xb; int Mc, m0, Nc, N; T scale;
+  cx<T>* Xb; int Mc, m0, Nc, N; T scale; FastDiv fNc;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
-    const int b = c / Nc, ni = c % Nc;
+    const int b = (int)fNc.div(c), ni = c - b * Nc;
     int m = (k <= (N - 1) / 2) ? k : k - N;
     int mi = m - m0;
     if (mi >= 0 && mi < Mc) Xb[((size_t)b * Mc + mi) * Nc + ni] = v * scale;
@@ -239,9 +244,9 @@ struct StRingNPair {
 // Inverse over m with Hermitian input and real output: columns g = 2c, 2c+1 packed.
 template <class T>
 struct LdRingMPair {
-  const cx<T>* Tb; int Mc, N, npair;
+  const cx<T>* Tb; int Mc, N, npair; FastDiv fP;
   __device__ cx<T> operator()(int c, int j) const {
-    const int b = c / npair, gp = c % npair, g1 = 2 * gp, g2 = g1 + 1;
+    const int b = (int)fP.div(c), gp = c - b * npair, g1 = 2 * gp, g2 = g1 + 1;
     const cx<T>* base = Tb + (size_t)b * Mc * N;
     int m = (j <= (N - 1) / 2) ? j : j - N;
     const int am = m < 0 ? -m : m;
@@ -253,9 +258,9 @@ struct LdRingMPair {
 };
 template <class T, class OutT>
 struct StWPair {
-  OutT* W; int N, npair;
+  OutT* W; int N, npair; FastDiv fP;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
-    const int b = c / npair, gp = c % npair, g1 = 2 * gp, g2 = g1 + 1;
+    const int b = (int)fP.div(c), gp = c - b * npair, g1 = 2 * gp, g2 = g1 + 1;
     const size_t idx = ((size_t)b * N + k) * N;
     W[idx + g1] = (OutT)v.re;
     if (g2 < N) W[idx + g2] = (OutT)v.im;
@@ -326,7 +331,7 @@ __device__ __forceinline__ cx<T> half_phase(int m, int N, T invN) {
 
 template <class T>
 __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int cpg, int Lb,
-                                                       const cx<T>* __restrict__ Xb, cx<T>* __restrict__ Y,
+                                                       FastDiv fgc, const cx<T>* __restrict__ Xb, cx<T>* __restrict__ Y,
                                                        ColSet cs, T scale, int pa, int pb, int pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, P = tb.P, Q = ct.Q, Tt = P >> 3, PL = padded_len(P);
@@ -338,14 +343,14 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) beta_quad_kernel(
   const T invN = (T)1 / (T)N;
   for (int c0 = blockIdx.x * Gc; c0 < ncols; c0 += gridDim.x * Gc) {
     for (int t = threadIdx.x; t < Gc * Lb; t += blockDim.x) {
-      const int b = t % Gc, j = t / Gc, c = c0 + b;
+      const int j = (int)fgc.div(t), b = t - j * Gc, c = c0 + b;
       tile[(size_t)b * CS + j] = (c < ncols) ? Xb[(size_t)j * ncols + c] : mk<T>(0, 0);
     }
     __syncthreads();
     for (int q = 0; q < cpg; ++q) {
       const int b = g * cpg + q, c = c0 + b;
       cx<T>* col = tile + (size_t)b * CS;
-      const int par = (c < ncols) ? ((cs.m_of(c) + cs.n_of(c) + cs.extra) & 1) : 0;
+      const int par = (c < ncols) ? cs.par(c) : 0;
       for (int j = tt; j < P; j += Tt) {
         cx<T> v = mk<T>(0, 0);
         if (j < Lb) v = col[j];
@@ -359,11 +364,11 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) beta_quad_kernel(
       // m'' >= 0 (same index) and the zero gap.
       for (int qi = Q - Lb + 1 + tt; qi < Q; qi += Tt) {
         const int mpp = qi - Q, k = mpp + N;
-        buf[padi(qi)] = buf[padi(k)] * chirp_of(tb, k, -1) * half_phase<T>(mpp, N, invN);
+        buf[padi(qi)] = buf[padi(k)] * chirp_of(tb, k, -1) * (conj(tb.hphase[k]) * invN);
       }
       __syncthreads();
       for (int qi = tt; qi <= Q - Lb; qi += Tt)
-        buf[padi(qi)] = (qi < Lb) ? buf[padi(qi)] * chirp_of(tb, qi, -1) * half_phase<T>(qi, N, invN) : mk<T>(0, 0);
+        buf[padi(qi)] = (qi < Lb) ? buf[padi(qi)] * chirp_of(tb, qi, -1) * (conj(tb.hphase[qi]) * invN) : mk<T>(0, 0);
       __syncthreads();
       fft_p2(buf, Q, ct.tw, -1, tt);
       for (int i = tt; i < Q; i += Tt) buf[padi(i)] = buf[padi(i)] * ct.what[i];
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) beta_quad_kernel(
       __syncthreads();
     }
     for (int t = threadIdx.x; t < Gc * Lb; t += blockDim.x) {
-      const int b = t % Gc, mp = t / Gc, c = c0 + b;
+      const int mp = (int)fgc.div(t), b = t - mp * Gc, c = c0 + b;
       if (c < ncols) Y[(size_t)mp * ncols + c] = tile[(size_t)b * CS + mp];
     }
     __syncthreads();
