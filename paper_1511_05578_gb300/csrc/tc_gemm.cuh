@@ -1,0 +1,249 @@
+// tcgen05 split-FP32 GEMM engine (sm_103a), shared by the Delta contractions and the
+// prime-factor DFTs of the mixed path.
+//
+// D[128 x BN] = sum_k A[128 x k] B[BN x k]^T with FP32 operands produced on the fly by a
+// problem object. Each operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a
+// K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM accumulator (split-FP32,
+// ~2^-22 per product). All 512 threads build the operand stage in shared memory in the
+// canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered;
+// one thread issues tcgen05.mma and commits to the stage's mbarrier; waits are bounded
+// and set an error flag instead of hanging; four warps drain TMEM with tcgen05.ld.
+#pragma once
+#include <cstdint>
+
+#include "transforms.cuh"
+
+namespace crv {
+namespace tc {
+
+constexpr int BM = 128, BK = 32, STAGES = 2, NT = 512;
+constexpr int A_BYTES = BM * BK * 4;             // 16 KB per A tile (hi or lo)
+constexpr long kWaitLimit = 1L << 22;            // bounded spin on mbarriers
+
+// Tile geometry for an accumulator of BN columns (BN in {64, 128, 192, 256}).
+template <int BN>
+struct Geo {
+  static constexpr int B_BYTES = BN * BK * 4;                       // B tile (hi or lo)
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2048;
+  static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+  // instruction descriptor: D f32, A/B tf32, K-major A and B, N = BN, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                    ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of the 16-byte chunk (row r, k-quad q) in a [rows x 32] tf32 tile:
+// core matrix (8 rows x 16 B) at (r/8, q); K-adjacent core matrices 128 B apart,
+// 8-row groups 1024 B apart.
+__device__ __forceinline__ uint32_t chunk_off(int r, int q) { return (uint32_t)((r >> 3) * 1024 + q * 128 + (r & 7) * 16); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128u >> 4) << 16;   // leading byte offset: next core matrix along K
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
+  return d;                           // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  for (long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 1);
+  return false;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Store four FP32 values as tf32 hi and lo into the (r, q) chunk of the hi and lo tiles.
+__device__ __forceinline__ void put4(unsigned char* hi_tile, unsigned char* lo_tile, int r, int q, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = tf32_rna(x[i]);
+    l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
+  }
+  const uint32_t off = chunk_off(r, q);
+  *reinterpret_cast<uint4*>(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a, int l, int b) {
+  const int ab = b < 0 ? -b : b;
+  float v = __ldg(Q + ((size_t)a * Lmax + l) * Lmax + ab);
+  return (b < 0 && ((l + a) & 1)) ? -v : v;
+}
+
+// ---------------------------------------------------------------------------
+// The GEMM kernel: one 128 x BN output tile per CTA.
+//   Prob::tile(z, r0, c0, kb, ke)             tile coordinates and K range from blockIdx
+//   Prob::a4(z, r0, k0, r, q, x[4])           A[r0 + r][k0 + 4q .. +3]
+//   Prob::b4(z, c0, k0, c, q, x[4])           B[c0 + c][k0 + 4q .. +3]
+//   Prob::store16(z, r0, c0, r, cc, d[16])    D[r0 + r][c0 + cc .. +15] (all 32 lanes call it)
+//   Prob::zero16(z, r0, c0, r, cc)            same for a tile with an empty K range
+// ---------------------------------------------------------------------------
+template <class Prob, int BN>
+__global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(Prob pb, int* err) {
+  using G = Geo<BN>;
+  constexpr int B_BYTES = G::B_BYTES, STAGE_BYTES = G::STAGE_BYTES;
+  extern __shared__ unsigned char smraw[];
+  const uint32_t raw = smem_u32(smraw);
+  unsigned char* base = smraw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned stage buffers
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  int mp, r0, c0g, kb, ke;
+  pb.tile(mp, r0, c0g, kb, ke);
+  const int nchunks = (ke > kb) ? (ke - kb + BK - 1) / BK : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % STAGES;
+    if (c >= STAGES) ok = mbar_wait(&bars[s], (uint32_t)((c / STAGES) - 1) & 1u, err) && ok;
+    unsigned char* st = base + s * STAGE_BYTES;
+    const int k0 = kb + c * BK;
+    // A: 128 rows x 8 k-quads, B: 256 rows x 8 k-quads; 2 + 4 chunks per thread.
+    // All loads of a thread are issued before any split/store (latency hiding).
+    {
+      constexpr int NA = BM * (BK / 4) / NT, NB = BN * (BK / 4) / NT;
+      float xa[NA][4], xb[NB][4];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const int it = tid + i * NT;
+        pb.a4(mp, r0, k0, it % BM, it / BM, xa[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const int it = tid + i * NT;
+        pb.b4(mp, c0g, k0, it % BN, it / BN, xb[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const int it = tid + i * NT;
+        put4(st, st + A_BYTES, it % BM, it / BM, xa[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < NB; ++i) {
+        const int it = tid + i * NT;
+        put4(st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, it % BN, it / BN, xb[i]);
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0 && ok) {
+      fence_after();
+      const uint32_t sa = smem_u32(st);
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        const uint32_t koff = ks * 256;  // two core matrices (8 tf32) per K-step
+        const uint64_t ahi = smem_desc(sa + koff), alo = smem_desc(sa + A_BYTES + koff);
+        const uint64_t bhi = smem_desc(sa + 2 * A_BYTES + koff), blo = smem_desc(sa + 2 * A_BYTES + B_BYTES + koff);
+        const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+        mma_tf32(tmem, alo, bhi, G::IDESC, first);
+        mma_tf32(tmem, ahi, blo, G::IDESC, 1u);
+        mma_tf32(tmem, ahi, bhi, G::IDESC, 1u);
+      }
+      mma_commit(&bars[s]);
+    }
+  }
+  if (nchunks > 0) {
+    const int last = nchunks - 1;
+    ok = mbar_wait(&bars[last % STAGES], (uint32_t)(last / STAGES) & 1u, err) && ok;
+  }
+  fence_after();
+  if (warp < 4) {
+    const int r = warp * 32 + (tid & 31);
+    for (int cc = 0; cc < BN; cc += 16) {
+      if (nchunks > 0 && ok) {
+        float d[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, d);
+        pb.store16(mp, r0, c0g, r, cc, d);
+      } else {
+        pb.zero16(mp, r0, c0g, r, cc);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace tc
+
+template <class Prob, int BN>
+bool launch_tc_gemm(const Prob& pb, dim3 grid, int* err, cudaStream_t st, int kind) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc::tc_gemm_kernel<Prob, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::Geo<BN>::SMEM_BYTES) != cudaSuccess)
+      return false;
+    attr = true;
+  }
+  KTimer kt(kind, st);
+  tc::tc_gemm_kernel<Prob, BN><<<grid, tc::NT, tc::Geo<BN>::SMEM_BYTES, st>>>(pb, err);
+  kt.done();
+  return launch_ok(kind_name(kind));
+}
+
+}  // namespace crv
