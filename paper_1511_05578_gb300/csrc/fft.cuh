@@ -1,164 +1,245 @@
-// Shared-memory FFT engine for the odd lengths N = 2L_j - 1 of the MW / SO(3)
-// grids (Eqs. nodes_alpha..nodes_gamma). A length-N DFT is done by Bluestein's
+// Register/shared-memory FFT engine for the odd lengths N = 2L_j - 1 of the MW and
+// SO(3) grids (Eqs. nodes_alpha..nodes_gamma). A length-N DFT is done by Bluestein's
 // chirp-z identity jk = (j^2 + k^2 - (k-j)^2)/2, which turns it into a cyclic
-// convolution of length P = 2^p >= 2N-1, done by a register-blocked Stockham
-// power-of-two FFT (radix-8 passes, one radix-4 or radix-2 pass when p is not a
-// multiple of 3). One code path serves every length (the prime factors of 2L-1
-// reach 89 at L = 1024).
+// convolution of length P = 2^p >= max(16, 2N-1), done with two power-of-two FFTs.
+// One code path serves every length (the prime factors of 2L-1 reach 89 at L = 1024).
 //
-// A transform is run by a group of P/8 threads (one radix-8 butterfly each per
-// pass); several groups share a block and all groups advance in lockstep, so
-// block-wide barriers separate the passes. Shared-memory indices are padded by
-// one element every 32 to break the bank conflicts of the strided passes.
+// Power-of-two FFT: Stockham autosort with 16 values per thread. TP = P/16 threads run
+// one transform; thread t holds x[t + q TP], q < 16, on entry AND on exit (natural
+// order both ways), so consecutive FFTs, pointwise products and the loads and stores
+// around them need no reordering. Stage 0 has radix R0 = 2^(p mod 4) (16 when 4 | p)
+// and no twiddles; every later stage has radix 16 and builds its twiddles from four
+// table values per thread.
+// Between two stages the values pass once through shared memory. Indices there are
+// padded by one element every 16, which leaves the exchanges of the P = 4096 transform
+// free of bank conflicts. Two exchange buffers alternate, so one barrier per exchange
+// suffices: a buffer is rewritten only after the barrier of the exchange in between.
 #pragma once
 #include "common.cuh"
 
 namespace crv {
 
-// Device tables for one length N, one precision.
+// Device tables of one length N in one precision.
 template <class T>
 struct DftTab {
   int N = 0, P = 0;
-  const cx<T>* tw = nullptr;      // [P]  e^{-2 pi i k / P}
+  int R0 = 16, nst = 1;           // radix of stage 0 and number of stages of the P-point FFT
+  const cx<T>* stw = nullptr;     // stage twiddles: stage s >= 1 (Ns = R0 16^(s-1) points done)
+                                  // holds [e][k] = e^{-2 pi i k 2^e / (16 Ns)}, e < 4, k < Ns,
+                                  // stages one after another
   const cx<T>* chirp = nullptr;   // [N]  h_t = e^{-i pi t^2 / N}
   const cx<T>* khat_f = nullptr;  // [P]  FFT_P(conj h wrapped) / P   (forward DFT, sign -1)
   const cx<T>* khat_i = nullptr;  // [P]  FFT_P(h wrapped) / P        (inverse DFT, sign +1)
   const cx<T>* hphase = nullptr;  // [N]  e^{+i pi m/N}, m = j (j < (N+1)/2) or j - N: half-sample phase of beta_b
 };
 
-// Power-of-two FFT tables of size Q (for the weight correlation of Eq. gmnmp).
+// Weight spectrum for the correlation of Eq. gmnmp (same P as the DftTab of the length).
 template <class T>
 struct CorrTab {
   int Q = 0;
-  const cx<T>* tw = nullptr;    // [Q] e^{-2 pi i k/Q}
   const cx<T>* what = nullptr;  // [Q] FFT_Q(v)/Q, v[t] = w(-t), t in (-(2L-1), 2L-1) wrapped
 };
 
-__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ int padded_len(int P) { return P + (P >> 5) + 1; }
 
-template <class T>
-__device__ __forceinline__ cx<T> ld_tw(const cx<T>* __restrict__ tw, int idx, int dir) {
-  cx<T> w = tw[idx];
-  return dir > 0 ? conj(w) : w;
+__host__ __device__ __forceinline__ int padx(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int xlen(int P) { return P + (P >> 4); }
+// Dynamic shared memory of an FFT block of NT threads: two exchange buffers of NT*16 values.
+template <class T> __host__ __device__ inline size_t fft_smem_bytes(int NT) {
+  return 2 * (size_t)xlen(16 * NT) * sizeof(cx<T>);
 }
 
-// In-register 8-point DFT (decimation in frequency), natural-order output.
+// One transform's exchange buffer: element i at p[padx(i) * s].
 template <class T>
-__device__ __forceinline__ void dft8(cx<T>* v, int dir) {
-  const T s = (T)0.70710678118654752440;
-  cx<T> a0 = v[0] + v[4], b0 = v[0] - v[4];
-  cx<T> a1 = v[1] + v[5], b1 = v[1] - v[5];
-  cx<T> a2 = v[2] + v[6], b2 = v[2] - v[6];
-  cx<T> a3 = v[3] + v[7], b3 = v[3] - v[7];
-  if (dir < 0) {
-    b1 = mk((b1.re + b1.im) * s, (b1.im - b1.re) * s);   // * e^{-i pi/4}
-    b2 = mk(b2.im, -b2.re);                              // * -i
-    b3 = mk((b3.im - b3.re) * s, -(b3.re + b3.im) * s);  // * e^{-3i pi/4}
-  } else {
-    b1 = mk((b1.re - b1.im) * s, (b1.re + b1.im) * s);
-    b2 = mk(-b2.im, b2.re);
-    b3 = mk(-(b3.re + b3.im) * s, (b3.re - b3.im) * s);
+struct XBuf {
+  cx<T>* p;
+  int s;
+  __device__ __forceinline__ cx<T>& operator[](int i) const { return p[(size_t)padx(i) * s]; }
+};
+// The two alternating buffers of one transform: buffer h starts at p + h * off.
+// take() hands out the next one.
+template <class T>
+struct XBuf2 {
+  cx<T>* p;
+  int s, off, cur;
+  __device__ __forceinline__ XBuf<T> take() {
+    XBuf<T> b{p + (cur ? off : 0), s};
+    cur ^= 1;
+    return b;
   }
-  cx<T> c0 = a0 + a2, c2 = a0 - a2, c1 = a1 + a3, d = a1 - a3;
-  cx<T> c3 = dir < 0 ? mk(d.im, -d.re) : mk(-d.im, d.re);
-  cx<T> e0 = b0 + b2, e2 = b0 - b2, e1 = b1 + b3, f = b1 - b3;
-  cx<T> e3 = dir < 0 ? mk(f.im, -f.re) : mk(-f.im, f.re);
-  v[0] = c0 + c1; v[4] = c0 - c1; v[2] = c2 + c3; v[6] = c2 - c3;
-  v[1] = e0 + e1; v[5] = e0 - e1; v[3] = e2 + e3; v[7] = e2 - e3;
+};
+
+template <int DIR, class T> __device__ __forceinline__ cx<T> rot(cx<T> a) {  // a * (DIR i)
+  return DIR < 0 ? mk(a.im, -a.re) : mk(-a.im, a.re);
+}
+template <int DIR, class T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, T c, T s) {  // a * (c + DIR i s)
+  const T ss = DIR < 0 ? -s : s;
+  return mk(a.re * c - a.im * ss, a.re * ss + a.im * c);
 }
 
-// Power-of-two Stockham FFT of one length-P sequence held in x (padded indices), in
-// place, run by the Tt = P/8 threads of a group (lane tt). P >= 8. All groups of
-// the block must call this together (block barriers between passes).
-// dir = -1: X_k = sum x_j e^{-2 pi i jk/P}; dir = +1: e^{+...} (no 1/P).
-template <class T>
-__device__ void fft_p2(cx<T>* x, int P, const cx<T>* __restrict__ tw, int dir, int tt) {
-  const int Q8 = P >> 3;
-  int Ns = 1;
-  while (Ns < P) {
-    const int R = P / Ns;
-    if (R >= 8) {
-      const int j = tt, k = j & (Ns - 1);
-      cx<T> v[8];
+// 4-point DFT in place, natural order, w = e^{DIR 2 pi i/4}; inputs NZ..3 are zero.
+template <int DIR, int NZ, class T>
+__device__ __forceinline__ void dft4(cx<T>& x0, cx<T>& x1, cx<T>& x2, cx<T>& x3) {
+  if constexpr (NZ == 1) {
+    x1 = x0; x2 = x0; x3 = x0;
+  } else {
+    cx<T> s0, d0, s1, d1;
+    if constexpr (NZ == 2) { s0 = x0; d0 = x0; s1 = x1; d1 = rot<DIR>(x1); }
+    else { s0 = x0 + x2; d0 = x0 - x2; s1 = x1 + x3; d1 = rot<DIR>(x1 - x3); }
+    x0 = s0 + s1; x2 = s0 - s1; x1 = d0 + d1; x3 = d0 - d1;
+  }
+}
+
+// 8-point DFT (one radix-2 split, then two 4-point DFTs); inputs NZ..7 are zero.
+template <int DIR, int NZ, class T>
+__device__ __forceinline__ void dft8(cx<T> (&x)[8]) {
+  const T c = (T)0.70710678118654752440;
+  cx<T> a[4], b[4];
 #pragma unroll
-      for (int r = 0; r < 8; ++r) v[r] = x[padi(j + r * Q8)];
-      if (Ns > 1) {
-        const int st = P / (8 * Ns);
-        const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = w1 * w1, w4 = w2 * w2;
-        const cx<T> w3 = w1 * w2, w5 = w1 * w4, w6 = w2 * w4, w7 = w3 * w4;
-        v[1] = v[1] * w1; v[2] = v[2] * w2; v[3] = v[3] * w3; v[4] = v[4] * w4;
-        v[5] = v[5] * w5; v[6] = v[6] * w6; v[7] = v[7] * w7;
+  for (int r = 0; r < 4; ++r) {
+    if constexpr (NZ == 8) { a[r] = x[r] + x[r + 4]; b[r] = x[r] - x[r + 4]; }
+    else { a[r] = x[r]; b[r] = x[r]; }
+  }
+  b[1] = cmulc<DIR>(b[1], c, c);
+  b[2] = rot<DIR>(b[2]);
+  b[3] = cmulc<DIR>(b[3], -c, c);
+  dft4<DIR, 4>(a[0], a[1], a[2], a[3]);
+  dft4<DIR, 4>(b[0], b[1], b[2], b[3]);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { x[2 * k] = a[k]; x[2 * k + 1] = b[k]; }
+}
+
+// 16-point DFT as 4 x 4: X[k1 + 4 k2] = sum_n2 w16^{n2 k1} w4^{n2 k2} sum_n1 x[4 n1 + n2] w4^{n1 k1}.
+// Inputs NZ..15 are zero (NZ = 16 or 8).
+template <int DIR, int NZ, class T>
+__device__ __forceinline__ void dft16(cx<T> (&x)[16]) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173, c2 = (T)0.70710678118654752440;
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<DIR, NZ / 4>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+  // y[n2][k1] sits at x[n2 + 4 k1]; twiddle w16^{n2 k1}
+  x[5] = cmulc<DIR>(x[5], c1, s1);      // 1
+  x[9] = cmulc<DIR>(x[9], c2, c2);      // 2
+  x[13] = cmulc<DIR>(x[13], s1, c1);    // 3
+  x[6] = cmulc<DIR>(x[6], c2, c2);      // 2
+  x[10] = rot<DIR>(x[10]);              // 4
+  x[14] = cmulc<DIR>(x[14], -c2, c2);   // 6
+  x[7] = cmulc<DIR>(x[7], s1, c1);      // 3
+  x[11] = cmulc<DIR>(x[11], -c2, c2);   // 6
+  x[15] = cmulc<DIR>(x[15], -c1, -s1);  // 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<DIR, 4>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  // X[k1 + 4 k2] sits at x[4 k1 + k2]
+  cx<T> y[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) y[i] = x[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = y[4 * k1 + k2];
+}
+
+// Stage 0: B = 16/R butterflies of radix R on v[i + r B], i < B. HIN: v[8..15] are zero.
+template <int DIR, int R, bool HIN, class T>
+__device__ __forceinline__ void stage0(cx<T> (&v)[16]) {
+  constexpr int B = 16 / R;
+  if constexpr (R == 16) {
+    dft16<DIR, HIN ? 8 : 16>(v);
+  } else if constexpr (R == 8) {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      cx<T> a[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) a[r] = v[i + r * B];
+      dft8<DIR, HIN ? 4 : 8>(a);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[i + r * B] = a[r];
+    }
+  } else if constexpr (R == 4) {
+#pragma unroll
+    for (int i = 0; i < B; ++i) dft4<DIR, HIN ? 2 : 4>(v[i], v[i + B], v[i + 2 * B], v[i + 3 * B]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+      if constexpr (HIN) {
+        v[i + B] = v[i];
+      } else {
+        const cx<T> a = v[i] + v[i + B], b = v[i] - v[i + B];
+        v[i] = a; v[i + B] = b;
       }
-      dft8(v, dir);
-      __syncthreads();
-      const int out = (j - k) * 8 + k;
-#pragma unroll
-      for (int r = 0; r < 8; ++r) x[padi(out + r * Ns)] = v[r];
-      __syncthreads();
-      Ns *= 8;
-    } else if (R == 4) {
-      cx<T> v[2][4];
-      const int Q4 = P >> 2;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = tt + h * Q8, k = j & (Ns - 1);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[h][r] = x[padi(j + r * Q4)];
-        if (Ns > 1) {
-          const int st = P / (4 * Ns);
-          const cx<T> w1 = ld_tw(tw, k * st, dir), w2 = ld_tw(tw, 2 * k * st, dir), w3 = ld_tw(tw, 3 * k * st, dir);
-          v[h][1] = v[h][1] * w1; v[h][2] = v[h][2] * w2; v[h][3] = v[h][3] * w3;
-        }
-        cx<T> a0 = v[h][0] + v[h][2], a1 = v[h][0] - v[h][2], a2 = v[h][1] + v[h][3], d = v[h][1] - v[h][3];
-        cx<T> a3 = dir < 0 ? mk(d.im, -d.re) : mk(-d.im, d.re);
-        v[h][0] = a0 + a2; v[h][1] = a1 + a3; v[h][2] = a0 - a2; v[h][3] = a1 - a3;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = tt + h * Q8, k = j & (Ns - 1), out = (j - k) * 4 + k;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) x[padi(out + r * Ns)] = v[h][r];
-      }
-      __syncthreads();
-      Ns *= 4;
-    } else {  // R == 2
-      cx<T> v[4][2];
-      const int Q2 = P >> 1;
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int j = tt + h * Q8, k = j & (Ns - 1);
-        v[h][0] = x[padi(j)];
-        v[h][1] = x[padi(j + Q2)];
-        if (Ns > 1) v[h][1] = v[h][1] * ld_tw(tw, k * (P / (2 * Ns)), dir);
-        cx<T> a = v[h][0] + v[h][1], b = v[h][0] - v[h][1];
-        v[h][0] = a; v[h][1] = b;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int j = tt + h * Q8, k = j & (Ns - 1), out = (j - k) * 2 + k;
-        x[padi(out)] = v[h][0];
-        x[padi(out + Ns)] = v[h][1];
-      }
-      __syncthreads();
-      Ns *= 2;
     }
   }
 }
 
-// Bluestein core on one sequence: on entry x[padi(j)] holds x_j h^sign_j for j < N
-// and 0 for N <= j < P; on exit x[padi(k)] holds the cyclic convolution with the
-// chirp kernel, so X_k = h^sign_k * x[padi(k)], k < N. Group-cooperative.
-template <class T>
-__device__ void bluestein_conv(cx<T>* x, const DftTab<T>& tb, int sign, int tt) {
-  const int P = tb.P, Tt = P >> 3;
-  fft_p2(x, P, tb.tw, -1, tt);
-  const cx<T>* kh = (sign < 0) ? tb.khat_f : tb.khat_i;
-  for (int i = tt; i < P; i += Tt) x[padi(i)] = x[padi(i)] * kh[i];
+// Exchange after a stage of radix R with Ns points done: output r of butterfly
+// j = t + i TP goes to (j - k) R + k + r Ns, k = j mod Ns; then thread t reads back
+// x[t + q TP]. One barrier between the writes and the reads (buffers alternate).
+template <int R, class T>
+__device__ __forceinline__ void exchange(cx<T> (&v)[16], XBuf<T> buf, int t, int TP, int Ns) {
+  constexpr int B = 16 / R;
+#pragma unroll
+  for (int i = 0; i < B; ++i) {
+    const int j = t + i * TP, k = j & (Ns - 1), base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[base + r * Ns] = v[i + r * B];
+  }
   __syncthreads();
-  fft_p2(x, P, tb.tw, +1, tt);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = buf[t + q * TP];
+}
+
+// Twiddles w^r, r < 16, of one radix-16 butterfly from the table values w, w^2, w^4,
+// w^8 (each r is a product of at most 4 of them: at most 3 roundings).
+template <class T>
+__device__ __forceinline__ void twiddles16(cx<T> w1, cx<T> w2, cx<T> w4, cx<T> w8, cx<T> (&w)[16]) {
+  w[1] = w1; w[2] = w2; w[4] = w4; w[8] = w8;
+  w[3] = w1 * w2; w[5] = w1 * w4; w[6] = w2 * w4; w[12] = w4 * w8;
+  w[7] = w[3] * w4; w[9] = w1 * w8; w[10] = w2 * w8; w[11] = w[3] * w8;
+  w[13] = w[5] * w8; w[14] = w[6] * w8; w[15] = w[7] * w8;
+}
+
+// In-register P-point FFT (no 1/P), w = e^{DIR 2 pi i/P}: v[q] = x[t + q TP] in and out.
+// All threads of the block call it together. HIN: x[j] = 0 for j >= P/2 (v[8..15] are
+// ignored).
+template <int DIR, bool HIN, class T>
+__device__ __forceinline__ void fft16(cx<T> (&v)[16], const DftTab<T>& tb, XBuf2<T>& buf, int t) {
+  const int TP = tb.P >> 4;
+  switch (tb.R0) {
+    case 16: stage0<DIR, 16, HIN>(v); break;
+    case 8: stage0<DIR, 8, HIN>(v); break;
+    case 4: stage0<DIR, 4, HIN>(v); break;
+    default: stage0<DIR, 2, HIN>(v); break;
+  }
+  if (tb.nst == 1) return;
+  int Ns = tb.R0;
+  const cx<T>* __restrict__ tw = tb.stw;
+  // base twiddles of stage 1, fetched before the barrier of the exchange
+  int k = t & (Ns - 1);
+  cx<T> b1 = tw[k], b2 = tw[Ns + k], b4 = tw[2 * Ns + k], b8 = tw[3 * Ns + k];
+  {
+    const XBuf<T> x = buf.take();
+    switch (tb.R0) {
+      case 16: exchange<16>(v, x, t, TP, 1); break;
+      case 8: exchange<8>(v, x, t, TP, 1); break;
+      case 4: exchange<4>(v, x, t, TP, 1); break;
+      default: exchange<2>(v, x, t, TP, 1); break;
+    }
+  }
+#pragma unroll 1
+  for (int s = 1; s < tb.nst; ++s) {
+    cx<T> w[16];
+    if (DIR > 0) { b1 = conj(b1); b2 = conj(b2); b4 = conj(b4); b8 = conj(b8); }
+    twiddles16(b1, b2, b4, b8, w);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = v[r] * w[r];
+    dft16<DIR, 16>(v);
+    if (s + 1 < tb.nst) {
+      tw += 4 * Ns;
+      const int Nn = Ns * 16;
+      k = t & (Nn - 1);
+      b1 = tw[k]; b2 = tw[Nn + k]; b4 = tw[2 * Nn + k]; b8 = tw[3 * Nn + k];
+      exchange<16>(v, buf.take(), t, TP, Ns);
+    }
+    Ns *= 16;
+  }
 }
 
 template <class T>

@@ -3,7 +3,8 @@
 //
 // Index sets of one transform of band limit Lb (N = 2Lb-1):
 //   m = m0 + mi, mi < Mc      (m0 = 0, Mc = Lb for real signals; m0 = -(Lb-1), Mc = N otherwise)
-//   n = n0 + nstep * ni, ni < Nc   (spin 0: even n only, nstep = 2; else nstep = 1)
+//   n = n0 + nstep * ni, ni < Nc   (spin 0: even n only, nstep = 2; else nstep = 1; the
+//                                   kernels rely on nstep being 1 or 2)
 //   m' = 0..Lb-1              (X_{m n, -m'} = (-1)^{m+n} X_{m n m'}, so only m' >= 0 is kept)
 // Volumes are stored [row][mi][ni] with ni fastest.
 #pragma once
@@ -26,76 +27,81 @@ struct ColSet {
 };
 
 // ---------------------------------------------------------------------------
-// Batched DFTs of length N (Bluestein, see fft.cuh). A block holds G groups of
-// P/8 threads; each group transforms one sequence at a time.
+// Batched DFTs of length N (Bluestein on the register FFT of fft.cuh). A block of
+// NT threads runs G = NT / TP transforms at a time, TP = P/16 threads each.
 //
-// rows_kernel: sequence c is gathered by ld(c, j), j < N, typically a contiguous
-//   row, so each group loads its own row (coalesced along j).
-// cols_kernel: consecutive sequences are adjacent in memory (columns); the block
-//   stages a tile of Gc = G*cpg columns in shared memory, loading and storing with
-//   the column index fastest (coalesced), and each group transforms cpg of them.
-// Storers get st(c, k, X_k, X_{(N-k) mod N}) for every k < N (the second value
-// serves the real-pair unpacking) and decide which outputs to keep.
+// COLS = false (rows): sequence c is gathered by ld(c, j), j < N, typically a
+//   contiguous row; a transform's threads are consecutive, so loads run along j.
+// COLS = true (columns): consecutive sequences are adjacent in memory; the G
+//   transforms of a block interleave their threads (g fastest), so each load or
+//   store touches G adjacent sequences, and the exchange buffers interleave too.
+// Storers get st(c, k, X_k, X_{(N-k) mod N}) for every k < N; the second value (the
+// real-pair unpacking) is gathered only for storers that declare kMirror.
 // ---------------------------------------------------------------------------
-template <class T, class Ld, class St>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) rows_kernel(DftTab<T> tb, int sign, int nrows, Ld ld, St st) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = tb.N, P = tb.P, Tt = P >> 3, PL = padded_len(P);
-  const int G = blockDim.x / Tt, g = threadIdx.x / Tt, tt = threadIdx.x % Tt;
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smraw) + (size_t)g * PL;
-  for (int r0 = blockIdx.x * G; r0 < nrows; r0 += gridDim.x * G) {
-    const int row = r0 + g;
-    const bool valid = row < nrows;
-    for (int j = tt; j < P; j += Tt) {
-      cx<T> v = mk<T>(0, 0);
-      if (valid && j < N) v = ld(row, j) * chirp_of(tb, j, sign);
-      buf[padi(j)] = v;
-    }
-    __syncthreads();
-    bluestein_conv(buf, tb, sign, tt);
-    if (valid) {
-      for (int k = tt; k < N; k += Tt) {
-        const int kn = (k == 0) ? 0 : N - k;
-        st(row, k, buf[padi(k)] * chirp_of(tb, k, sign), buf[padi(kn)] * chirp_of(tb, kn, sign));
-      }
-    }
-    __syncthreads();
-  }
+template <class St> struct Mirror { static constexpr bool value = false; };
+
+template <class T, int NT, bool COLS>
+__device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned char* smraw, int P) {
+  const int TP = P >> 4, G = NT / TP, XL = xlen(P);
+  cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
+  if (COLS) { g = threadIdx.x % G; t = threadIdx.x / G; }
+  else { g = threadIdx.x / TP; t = threadIdx.x % TP; }
+  buf.p = COLS ? sm + g : sm + (size_t)g * XL;
+  buf.s = COLS ? G : 1;
+  buf.off = G * XL;
+  buf.cur = 0;
 }
 
-template <class T, class Ld, class St>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) cols_kernel(DftTab<T> tb, int sign, int ncols, int cpg,
-                                                                          FastDiv fgc, Ld ld, St st) {
+// Blocks of NT threads; FP32 blocks of 256 threads fit twice on an SM (<= 128 registers).
+template <class T, int NT> struct FftMinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1; };
+
+template <class T, int NT, bool COLS, class Ld, class St>
+__global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(DftTab<T> tb, int sign, int nseq, Ld ld, St st) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = tb.N, P = tb.P, Tt = P >> 3, PL = padded_len(P);
-  const int G = blockDim.x / Tt, g = threadIdx.x / Tt, tt = threadIdx.x % Tt;
-  const int Gc = G * cpg;
-  const int CS = N | 1;                                     // odd column stride: no bank conflicts
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smraw);          // [Gc][CS]
-  cx<T>* buf = tile + (size_t)Gc * CS + (size_t)g * PL;    // per group work buffer
-  for (int c0 = blockIdx.x * Gc; c0 < ncols; c0 += gridDim.x * Gc) {
-    for (int t = threadIdx.x; t < Gc * N; t += blockDim.x) {
-      const int j = (int)fgc.div(t), b = t - j * Gc, c = c0 + b;
-      tile[(size_t)b * CS + j] = (c < ncols) ? ld(c, j) : mk<T>(0, 0);
+  const int N = tb.N, TP = tb.P >> 4, G = NT / TP;
+  int g, t;
+  XBuf2<T> buf;
+  fft_slot<T, NT, COLS>(g, t, buf, smraw, tb.P);
+  const cx<T>* __restrict__ kh = (sign < 0) ? tb.khat_f : tb.khat_i;
+  for (int s0 = blockIdx.x * G; s0 < nseq; s0 += gridDim.x * G) {
+    const int c = s0 + g;
+    const bool valid = c < nseq;
+    cx<T> v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {  // j < N <= P/2 only for q < 8
+      const int j = t + q * TP;
+      v[q] = mk<T>(0, 0);
+      if (q < 8 && valid && j < N) v[q] = ld(c, j) * chirp_of(tb, j, sign);
     }
-    __syncthreads();
-    for (int q = 0; q < cpg; ++q) {
-      const int b = g * cpg + q;
-      cx<T>* col = tile + (size_t)b * CS;
-      for (int j = tt; j < P; j += Tt) buf[padi(j)] = (j < N) ? col[j] * chirp_of(tb, j, sign) : mk<T>(0, 0);
-      __syncthreads();
-      bluestein_conv(buf, tb, sign, tt);
-      for (int k = tt; k < N; k += Tt) col[k] = buf[padi(k)] * chirp_of(tb, k, sign);
-      __syncthreads();
+    fft16<-1, true>(v, tb, buf, t);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * kh[t + q * TP];
+    fft16<+1, false>(v, tb, buf, t);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = t + q * TP;
+      v[q] = v[q] * chirp_of(tb, k < N ? k : 0, sign);
     }
-    for (int t = threadIdx.x; t < Gc * N; t += blockDim.x) {
-      const int k = (int)fgc.div(t), b = t - k * Gc, c = c0 + b;
-      if (c < ncols) {
-        const int kn = (k == 0) ? 0 : N - k;
-        st(c, k, tile[(size_t)b * CS + k], tile[(size_t)b * CS + kn]);
+    if constexpr (Mirror<St>::value) {
+      const XBuf<T> x = buf.take();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = t + q * TP;
+        if (k < N) x[k] = v[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = t + q * TP;
+        if (valid && k < N) st(c, k, v[q], x[k == 0 ? 0 : N - k]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = t + q * TP;
+        if (valid && k < N) st(c, k, v[q], v[q]);
       }
     }
-    __syncthreads();
   }
 }
 
@@ -131,8 +137,8 @@ struct LdRingN {
     // j = n mod N; find ni with n0 + nstep*ni == n
     int n = (j <= (N - 1) / 2) ? j : j - N;
     int d = n - n0;
-    if (d < 0 || d % nstep) return mk<T>(0, 0);
-    int ni = d / nstep;
+    if (d < 0 || (d & (nstep - 1))) return mk<T>(0, 0);
+    const int ni = d >> (nstep - 1);
     if (ni >= Nc) return mk<T>(0, 0);
     return Xb[(size_t)c * Nc + ni];
   }
@@ -188,8 +194,8 @@ struct StRingN {  // U[c][ni] = D[n mod N] / N for n in the n-set
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
     int n = (k <= (N - 1) / 2) ? k : k - N;
     int d = n - n0;
-    if (d < 0 || d % nstep) return;
-    int ni = d / nstep;
+    if (d < 0 || (d & (nstep - 1))) return;
+    const int ni = d >> (nstep - 1);
     if (ni < Nc) U[(size_t)c * Nc + ni] = v * scale;
   }
 };
@@ -231,8 +237,8 @@ struct StRingNPair {
   __device__ void operator()(int c, int k, cx<T> z, cx<T> zn) const {
     int n = (k <= (N - 1) / 2) ? k : k - N;
     int d = n - n0;
-    if (d < 0 || d % nstep) return;
-    int ni = d / nstep;
+    if (d < 0 || (d & (nstep - 1))) return;
+    const int ni = d >> (nstep - 1);
     if (ni >= Nc) return;
     const T h = scale * (T)0.5;
     const cx<T> a = mk<T>((z.re + zn.re) * h, (z.im - zn.im) * h);   // (z + conj zn)/2
@@ -241,6 +247,7 @@ struct StRingNPair {
     if (2 * c + 1 < nrows) U[(size_t)(2 * c + 1) * Nc + ni] = b;
   }
 };
+template <class T> struct Mirror<StRingNPair<T>> { static constexpr bool value = true; };
 // Inverse over m with Hermitian input and real output: columns g = 2c, 2c+1 packed.
 template <class T>
 struct LdRingMPair {
@@ -318,81 +325,80 @@ struct StMapRow {
 // (precomputed transform of v[t] = w(-t) on Q = P points), fold
 // Yhat_{m'} = Y_{m'} + (-1)^{m+n+extra} Y_{-m'} (m' > 0), and multiply by
 // scale * i^{m*pa + n*pb + pc}. In: Xb[b][c] (b < Lb); out: Y[m'][c] (m' < Lb).
-// Same tiling as cols_kernel.
+// Threads laid out as in dft_kernel with COLS = true.
 // ---------------------------------------------------------------------------
-// e^{-i m pi/N} / N
-template <class T>
-__device__ __forceinline__ cx<T> half_phase(int m, int N, T invN) {
-  T s, co;
-  if (sizeof(T) == 8) { double sd, cd; sincospi(-(double)m / (double)N, &sd, &cd); s = (T)sd; co = (T)cd; }
-  else { float sf, cf; sincospif(-(float)m / (float)N, &sf, &cf); s = (T)sf; co = (T)cf; }
-  return mk(co * invN, s * invN);
-}
-
-template <class T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int cpg, int Lb,
-                                                       FastDiv fgc, const cx<T>* __restrict__ Xb, cx<T>* __restrict__ Y,
-                                                       ColSet cs, T scale, int pa, int pb, int pc) {
+template <class T, int NT>
+__global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int Lb,
+                                                                    const cx<T>* __restrict__ Xb,
+                                                                    cx<T>* __restrict__ Y, ColSet cs, T scale, int pa,
+                                                                    int pb, int pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = tb.N, P = tb.P, Q = ct.Q, Tt = P >> 3, PL = padded_len(P);
-  const int G = blockDim.x / Tt, g = threadIdx.x / Tt, tt = threadIdx.x % Tt;
-  const int Gc = G * cpg;
-  const int CS = Lb | 1;                           // odd column stride: no bank conflicts
-  cx<T>* tile = reinterpret_cast<cx<T>*>(smraw);  // [Gc][CS]
-  cx<T>* buf = tile + (size_t)Gc * CS + (size_t)g * PL;
+  const int N = tb.N, Q = ct.Q, TP = tb.P >> 4, G = NT / TP;
+  int g, t;
+  XBuf2<T> buf;
+  fft_slot<T, NT, true>(g, t, buf, smraw, tb.P);
   const T invN = (T)1 / (T)N;
-  for (int c0 = blockIdx.x * Gc; c0 < ncols; c0 += gridDim.x * Gc) {
-    for (int t = threadIdx.x; t < Gc * Lb; t += blockDim.x) {
-      const int j = (int)fgc.div(t), b = t - j * Gc, c = c0 + b;
-      tile[(size_t)b * CS + j] = (c < ncols) ? Xb[(size_t)j * ncols + c] : mk<T>(0, 0);
+  for (int s0 = blockIdx.x * G; s0 < ncols; s0 += gridDim.x * G) {
+    const int c = s0 + g;
+    const bool valid = c < ncols;
+    const int par = valid ? cs.par(c) : 0;
+    // extension to the 2Lb-1 nodes of the full circle, then the chirp
+    cx<T> v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int j = t + q * TP;
+      v[q] = mk<T>(0, 0);
+      if (q < 8 && valid && j < N) {
+        cx<T> x = Xb[(size_t)(j < Lb ? j : N - 1 - j) * ncols + c];
+        if (j >= Lb && par) x = mk(-x.re, -x.im);
+        v[q] = x * chirp_of(tb, j, -1);
+      }
+    }
+    fft16<-1, true>(v, tb, buf, t);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * tb.khat_f[t + q * TP];
+    fft16<+1, false>(v, tb, buf, t);
+    // u_{m''} at index m'' mod Q: D_{m'' mod N} h_k e^{-i m'' pi/N} / N; zero for Lb <= index <= Q - Lb
+    {
+      const XBuf<T> x = buf.take();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int k = t + q * TP;
+        if (q < 8 && k < N) x[k < Lb ? k : k - N + Q] = v[q] * chirp_of(tb, k, -1) * (conj(tb.hphase[k]) * invN);
+        if (k >= Lb && k <= Q - Lb) x[k] = mk<T>(0, 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = x[t + q * TP];
+    }
+    fft16<-1, false>(v, tb, buf, t);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * ct.what[t + q * TP];
+    fft16<+1, false>(v, tb, buf, t);
+    // fold Yhat_{m'} = Y_{m'} + (-1)^{par} Y_{-m'}, phase and scale
+    const XBuf<T> y = buf.take();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = t + q * TP;
+      if (i > Q - Lb) y[i] = v[q];
     }
     __syncthreads();
-    for (int q = 0; q < cpg; ++q) {
-      const int b = g * cpg + q, c = c0 + b;
-      cx<T>* col = tile + (size_t)b * CS;
-      const int par = (c < ncols) ? cs.par(c) : 0;
-      for (int j = tt; j < P; j += Tt) {
-        cx<T> v = mk<T>(0, 0);
-        if (j < Lb) v = col[j];
-        else if (j < N) { v = col[N - 1 - j]; if (par) v = mk(-v.re, -v.im); }
-        buf[padi(j)] = v * chirp_of(tb, j < N ? j : 0, -1);
-      }
-      __syncthreads();
-      bluestein_conv(buf, tb, -1, tt);
-      // u_{m''} at index m'' mod Q: D_{m'' mod N} h_k e^{-i m'' pi/N} / N, in place in two
-      // phases: the negative m'' (sources k in [Lb, N), targets q >= N, disjoint), then
-      // m'' >= 0 (same index) and the zero gap.
-      for (int qi = Q - Lb + 1 + tt; qi < Q; qi += Tt) {
-        const int mpp = qi - Q, k = mpp + N;
-        buf[padi(qi)] = buf[padi(k)] * chirp_of(tb, k, -1) * (conj(tb.hphase[k]) * invN);
-      }
-      __syncthreads();
-      for (int qi = tt; qi <= Q - Lb; qi += Tt)
-        buf[padi(qi)] = (qi < Lb) ? buf[padi(qi)] * chirp_of(tb, qi, -1) * (conj(tb.hphase[qi]) * invN) : mk<T>(0, 0);
-      __syncthreads();
-      fft_p2(buf, Q, ct.tw, -1, tt);
-      for (int i = tt; i < Q; i += Tt) buf[padi(i)] = buf[padi(i)] * ct.what[i];
-      __syncthreads();
-      fft_p2(buf, Q, ct.tw, +1, tt);
-      if (c < ncols) {
-        const int m = cs.m_of(c), n = cs.n_of(c);
-        const int ph = imod(m * pa + n * pb + pc, 4);
-        for (int mp = tt; mp < Lb; mp += Tt) {
-          cx<T> v = buf[padi(mp)];
+    if (valid) {
+      const int m = cs.m_of(c), n = cs.n_of(c);
+      const int ph = imod(m * pa + n * pb + pc, 4);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int mp = t + q * TP;
+        if (mp < Lb) {
+          cx<T> val = v[q];
           if (mp > 0) {
-            const cx<T> w = buf[padi(Q - mp)];
-            v = par ? v - w : v + w;
+            const cx<T> w = y[Q - mp];
+            val = par ? val - w : val + w;
           }
-          col[mp] = mul_ipow(v * scale, ph);
+          Y[(size_t)mp * ncols + c] = mul_ipow(val * scale, ph);
         }
       }
-      __syncthreads();
     }
-    for (int t = threadIdx.x; t < Gc * Lb; t += blockDim.x) {
-      const int mp = (int)fgc.div(t), b = t - mp * Gc, c = c0 + b;
-      if (c < ncols) Y[(size_t)mp * ncols + c] = tile[(size_t)b * CS + mp];
-    }
-    __syncthreads();
   }
 }
 
