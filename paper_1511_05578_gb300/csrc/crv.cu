@@ -15,6 +15,7 @@
 
 #include "../../include/crv.h"
 #include "contract.cuh"
+#include "tc_contract.cuh"
 
 namespace crv {
 
@@ -86,11 +87,6 @@ static int fail(int code, const std::string& msg) { g_err = msg; return code; }
 void set_error(const std::string& msg) { g_err = msg; }
 
 cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_e, cudaStream_t st);
-// tensor-core contractions (tc_contract.cu)
-bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, const float* psi, int Lb, ColSet cs,
-                 cx<float>* X, int* err, cudaStream_t st);
-bool tc_synthesis(const float* Q32, const double* Q64, int Lmax, const cx<float>* Y, const float* psi, int Lb,
-                  ColSet cs, cx<float>* Zscratch, cx<double>* flm, int* err, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Host numerics for the plan tables
@@ -243,6 +239,7 @@ struct crv_plan_s {
   void* wXb = nullptr;
   void* wR = nullptr;
   bool use_tc = false;   // tensor-core contractions (mixed plans)
+  std::vector<TcTab> tabA, tabS;  // per scale: B operand tables of the two contractions
   int* d_err = nullptr;   // set by kernels whose bounded waits gave up
   size_t vol_bytes = 0, ring_bytes = 0;
   std::vector<void*> allocs;
@@ -399,12 +396,12 @@ static int num_sms() {
 
 // Persistent FFT blocks (one or two per SM, by shared memory and registers), each
 // looping over groups of G sequences.
-template <class T, int NT, bool COLS, class Ld, class St>
+template <class T, int NT, bool COLS, int PT, bool SPAN, class Ld, class St>
 static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld, St st, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
-  auto kern = dft_kernel<T, NT, COLS, Ld, St>;
+  auto kern = dft_kernel<T, NT, COLS, PT, SPAN, Ld, St>;
   if (!set_smem(kern, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
   const int grid = std::max(1, std::min((nseq + G - 1) / G, num_sms() * bps));
@@ -413,12 +410,20 @@ static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld,
   kt.done();
   return launch_ok(kind_name(kind));
 }
-template <class T, bool COLS, class Ld, class St>
+// WIDE: columns of a large volume (the beta transforms over all (m, n)), read from HBM:
+// two adjacent columns per block and a contiguous run of columns per block (reuse of
+// each sector through L1). Ring columns (read from the L2-resident ring buffer, written
+// into the large W or Xb volumes) and rows run faster with two 256-thread blocks per SM
+// striding together, so that each output sector is filled at about one time (measured).
+template <class T, bool COLS, bool WIDE = false, class Ld, class St>
 static bool run_dft(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld, St st, cudaStream_t s) {
   if (nseq <= 0) return true;
-  // 256 threads: two blocks per SM for FP32 (rows and columns measured no slower than
-  // with 512), one for FP64
-  return run_dft_nt<T, 256, COLS>(kind, tb, sign, nseq, ld, st, s);
+  // FP32: 256 threads (two blocks per SM), 512 for WIDE columns. FP64: 256 threads, one
+  // block per SM. The lengths of the two largest band limits get kernels compiled for their P.
+  constexpr int NT = (sizeof(T) == 4 && COLS && WIDE) ? 512 : 256;
+  if (sizeof(T) == 4 && tb.P == 4096) return run_dft_nt<T, NT, COLS, 4096, WIDE>(kind, tb, sign, nseq, ld, st, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_dft_nt<T, NT, COLS, 2048, WIDE>(kind, tb, sign, nseq, ld, st, s);
+  return run_dft_nt<T, NT, COLS, 0, WIDE>(kind, tb, sign, nseq, ld, st, s);
 }
 template <class T, class Ld, class St>
 static bool run_rows(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
@@ -428,18 +433,22 @@ template <class T, class Ld, class St>
 static bool run_cols(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
   return run_dft<T, true>(kind, tb, sign, n, ld, st, s);
 }
+template <class T, class Ld, class St>
+static bool run_cols_wide(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
+  return run_dft<T, true, true>(kind, tb, sign, n, ld, st, s);
+}
 
-template <class T, int NT>
+template <class T, int NT, int PT>
 static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y,
                              ColSet cs, T scale, int pa, int pb, int pc, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
-  if (!set_smem(beta_quad_kernel<T, NT>, smem)) return false;
+  if (!set_smem(beta_quad_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
   const int grid = std::max(1, std::min((ncols + G - 1) / G, num_sms() * bps));
   KTimer kt(K_BETA_QUAD, s);
-  beta_quad_kernel<T, NT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc);
+  beta_quad_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc);
   kt.done();
   return launch_ok("beta_quad_kernel");
 }
@@ -450,7 +459,10 @@ static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, 
   const CorrTab<T>& ct = corr_of<T>(fs);
   if (ct.Q != tb.P) { g_err = "beta quadrature needs Q == P"; return false; }
   if (ncols <= 0) return true;
-  return run_beta_quad_nt<T, 256>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
+  constexpr int NT = sizeof(T) == 4 ? 512 : 256;
+  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
+  return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -524,7 +536,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   bool used_tc = false;
   if constexpr (sizeof(T) == 4) {
     if (p->use_tc) {
-      if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->dpsi32[j], Lb, cs, (cx<float>*)X, p->d_err, st)) return false;
+      if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->tabA[j], Lb, cs, (cx<float>*)X, p->d_err, st)) return false;
       used_tc = true;
     }
   }
@@ -536,7 +548,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase},
+  if (!run_cols_wide<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase},
                          StRows<T>{Xb, ncols, Lb}, st))
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
@@ -591,8 +603,8 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   if constexpr (sizeof(T) == 4) {
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
     if (p->use_tc)
-      return tc_synthesis(p->dQ32, p->dQ, p->L, (const cx<float>*)Y, p->dpsi32[j], Lb, cs, (cx<float>*)p->wXb, flm,
-                          p->d_err, st);
+      return tc_synthesis(p->dQ, p->L, (const cx<float>*)Y, p->tabS[j], Lb, cs, (cx<float>*)p->wXb, flm, p->d_err,
+                          st);
   }
   const int mchunk = 16;
   dim3 g((Lb + 31) / 32, (cs.Mc + 31) / 32, (Lb + mchunk - 1) / mchunk);
@@ -710,6 +722,44 @@ int crv_profile_reset(void) {
   std::lock_guard<std::mutex> g(g_prof.mu);
   g_prof.drain(g_prof.pending.size());
   for (int k = 0; k < K_NKINDS; ++k) { g_prof.launches[k] = 0; g_prof.ms[k] = 0; }
+  return CRV_OK;
+}
+
+// B operand tables of the tensor-core contractions, per scale (Delta Psi in the engine's
+// tile layout; see tc_contract.cuh).
+static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
+  int stt = CRV_OK;
+  p->tabA.assign(p->J + 1, TcTab());
+  p->tabS.assign(p->J + 1, TcTab());
+  for (int j = p->J0; j <= p->J; ++j) {
+    const int Lb = p->Lj[j];
+    const ColSet cs = p->colset(Lb);
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<int2> range;
+      int ntiles = 0;
+      if (dir == 0) tc_analysis_ranges(Lb, cs, range, ntiles);
+      else tc_synthesis_ranges(Lb, cs, range, ntiles);
+      std::vector<long long> base(range.size());
+      long long total = 0;
+      for (size_t i = 0; i < range.size(); ++i) {
+        base[i] = total - range[i].x;
+        total += range[i].y;
+      }
+      float* data = p->dalloc<float>((size_t)std::max<long long>(total, 1) * TC_CHUNK_FLOATS, &stt);
+      long long* dbase = p->dalloc<long long>(base.size(), &stt);
+      int2* drange = p->dalloc<int2>(range.size(), &stt);
+      if (stt != CRV_OK) return stt;
+      cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
+      cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
+      TcTab t;
+      t.data = data; t.base = dbase; t.range = drange; t.ntiles = ntiles;
+      const bool ok = dir == 0 ? tc_fill_analysis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, data, st)
+                               : tc_fill_synthesis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, data, st);
+      if (!ok) return CRV_ECUDA;
+      (dir == 0 ? p->tabA : p->tabS)[j] = t;
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CRV_ECUDA, "contraction table build failed");
   return CRV_OK;
 }
 
@@ -843,6 +893,10 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
     std::string m = std::string("Delta table build failed: ") + cudaGetErrorString(e) + " " + g_err;
     delete p;
     return fail(CRV_ECUDA, m);
+  }
+  if (p->use_tc) {
+    const int rc = build_tc_tables(p, st);
+    if (rc != CRV_OK) { delete p; return rc; }
   }
   *out = p;
   return CRV_OK;

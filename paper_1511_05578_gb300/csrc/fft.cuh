@@ -196,42 +196,62 @@ __device__ __forceinline__ void twiddles16(cx<T> w1, cx<T> w2, cx<T> w4, cx<T> w
   w[13] = w[5] * w8; w[14] = w[6] * w8; w[15] = w[7] * w8;
 }
 
-// In-register P-point FFT (no 1/P), w = e^{DIR 2 pi i/P}: v[q] = x[t + q TP] in and out.
-// All threads of the block call it together. HIN: x[j] = 0 for j >= P/2 (v[8..15] are
-// ignored).
+// Stage structure of a P-point FFT (P = 2^p >= 16): radix of stage 0 and number of stages.
+__host__ __device__ constexpr int fft_log2(int P) { return P <= 1 ? 0 : 1 + fft_log2(P >> 1); }
+__host__ __device__ constexpr int fft_r0(int P) { return (fft_log2(P) % 4) ? (1 << (fft_log2(P) % 4)) : 16; }
+__host__ __device__ constexpr int fft_nst(int P) {
+  return 1 + (fft_log2(P) - (fft_r0(P) == 16 ? 4 : fft_log2(P) % 4)) / 4;
+}
+
 template <int DIR, bool HIN, class T>
-__device__ __forceinline__ void fft16(cx<T> (&v)[16], const DftTab<T>& tb, XBuf2<T>& buf, int t) {
-  const int TP = tb.P >> 4;
-  switch (tb.R0) {
+__device__ __forceinline__ void stage0_rt(cx<T> (&v)[16], int R0) {
+  switch (R0) {
     case 16: stage0<DIR, 16, HIN>(v); break;
     case 8: stage0<DIR, 8, HIN>(v); break;
     case 4: stage0<DIR, 4, HIN>(v); break;
     default: stage0<DIR, 2, HIN>(v); break;
   }
-  if (tb.nst == 1) return;
-  int Ns = tb.R0;
+}
+template <class T>
+__device__ __forceinline__ void exchange0_rt(cx<T> (&v)[16], XBuf<T> x, int t, int TP, int R0) {
+  switch (R0) {
+    case 16: exchange<16>(v, x, t, TP, 1); break;
+    case 8: exchange<8>(v, x, t, TP, 1); break;
+    case 4: exchange<4>(v, x, t, TP, 1); break;
+    default: exchange<2>(v, x, t, TP, 1); break;
+  }
+}
+
+// In-register P-point FFT (no 1/P), w = e^{DIR 2 pi i/P}: v[q] = x[t + q TP] in and out.
+// All threads of the block call it together. HIN: x[j] = 0 for j >= P/2 (v[8..15] are
+// ignored). PT = P as a compile-time constant (the stage loop unrolls and every index
+// folds), or 0 to take P from the table.
+template <int DIR, bool HIN, int PT, class T>
+__device__ __forceinline__ void fft16(cx<T> (&v)[16], const DftTab<T>& tb, XBuf2<T>& buf, int t) {
+  const int P = PT ? PT : tb.P;
+  const int TP = P >> 4;
+  const int R0 = PT ? fft_r0(PT) : tb.R0;
+  const int nst = PT ? fft_nst(PT) : tb.nst;
+  if constexpr (PT != 0) stage0<DIR, fft_r0(PT), HIN>(v);
+  else stage0_rt<DIR, HIN>(v, R0);
+  if (nst == 1) return;
+  int Ns = R0;
   const cx<T>* __restrict__ tw = tb.stw;
   // base twiddles of stage 1, fetched before the barrier of the exchange
   int k = t & (Ns - 1);
   cx<T> b1 = tw[k], b2 = tw[Ns + k], b4 = tw[2 * Ns + k], b8 = tw[3 * Ns + k];
-  {
-    const XBuf<T> x = buf.take();
-    switch (tb.R0) {
-      case 16: exchange<16>(v, x, t, TP, 1); break;
-      case 8: exchange<8>(v, x, t, TP, 1); break;
-      case 4: exchange<4>(v, x, t, TP, 1); break;
-      default: exchange<2>(v, x, t, TP, 1); break;
-    }
-  }
-#pragma unroll 1
-  for (int s = 1; s < tb.nst; ++s) {
+  if constexpr (PT != 0) exchange<fft_r0(PT)>(v, buf.take(), t, TP, 1);
+  else exchange0_rt(v, buf.take(), t, TP, R0);
+  // radix-16 stage s: twiddles from the prefetched base values, butterfly, and (not
+  // after the last stage) the next base values and the exchange
+  auto stage = [&](int s) {
     cx<T> w[16];
     if (DIR > 0) { b1 = conj(b1); b2 = conj(b2); b4 = conj(b4); b8 = conj(b8); }
     twiddles16(b1, b2, b4, b8, w);
 #pragma unroll
     for (int r = 1; r < 16; ++r) v[r] = v[r] * w[r];
     dft16<DIR, 16>(v);
-    if (s + 1 < tb.nst) {
+    if (s + 1 < nst) {
       tw += 4 * Ns;
       const int Nn = Ns * 16;
       k = t & (Nn - 1);
@@ -239,6 +259,13 @@ __device__ __forceinline__ void fft16(cx<T> (&v)[16], const DftTab<T>& tb, XBuf2
       exchange<16>(v, buf.take(), t, TP, Ns);
     }
     Ns *= 16;
+  };
+  if constexpr (PT != 0) {
+#pragma unroll
+    for (int s = 1; s < fft_nst(PT); ++s) stage(s);
+  } else {
+#pragma unroll 1
+    for (int s = 1; s < nst; ++s) stage(s);
   }
 }
 

@@ -10,31 +10,39 @@
 //
 // Each FP32 operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a K-step issues
 // hi*hi + hi*lo + lo*hi into the same FP32 TMEM accumulator (split-FP32, ~2^-22 per
-// product). Operands are built on the fly by all 256 threads into shared memory in the
-// canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered;
-// one thread issues tcgen05.mma and commits to an mbarrier per stage; waits are bounded
-// and set an error flag instead of hanging. The accumulator tile is 128 lanes x 128
-// columns of TMEM, drained by four warps with tcgen05.ld.
+// product). The B operand (Delta Psi, independent of the signal) comes from tables
+// built once per plan in the engine's canonical layout; the A operand is built on the
+// fly. See tc_gemm.cuh for the pipeline.
+#include "tc_contract.cuh"
 #include "tc_gemm.cuh"
 
 namespace crv {
 namespace tc {
 
 constexpr int BNC = 256;  // accumulator width of the contraction tiles
+static_assert(BNC == TC_TILE_ROWS, "table tiles are accumulator tiles");
 
 // ---------------------------------------------------------------------------
 // Problems: operand builders, K ranges and epilogues
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void tab4(const TcTab& tb, int mp, int tile, int k0, int c, int q, float* x) {
+  const long long chunk = tb.base[mp * tb.ntiles + tile] + (k0 >> 5);
+  const float4 v = __ldg(reinterpret_cast<const float4*>(tb.data + (size_t)chunk * TC_CHUNK_FLOATS + (c >> 3) * 256 +
+                                                         q * 32 + (c & 7) * 4));
+  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+}
+
 struct AnalysisProb {
-  const float* Q; int Lmax; const cx<float>* flm; const float* psi; int Lb; ColSet cs; cx<float>* X;
+  const float* Q; int Lmax; const cx<float>* flm; TcTab tb; int Lb; ColSet cs; cx<float>* X;
+  // K chunks: the table's run for (m', n-tile), skipping chunks below min |m| of the m-tile
   __device__ void tile(int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
     mp = blockIdx.z; mi0 = blockIdx.y * (BM / 2); n0i = blockIdx.x * BNC;
     const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
-    const int nlo = cs.n0 + cs.nstep * n0i, nhi = cs.n0 + cs.nstep * (min(n0i + BNC, cs.Nc) - 1);
     const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
-    const int bmin = (nlo <= 0 && nhi >= 0) ? 0 : min(abs(nlo), abs(nhi));
-    kb = max(mp, max(amin, bmin));
-    ke = Lb;
+    const int2 rg = tb.range[mp * tb.ntiles + blockIdx.x];
+    const int c0 = max(rg.x, amin >> 5), c1 = rg.x + rg.y;
+    kb = c0 * TC_CHUNK_K;
+    ke = max(c0, c1) * TC_CHUNK_K;
   }
   // A chunk: row r = 2 (m - mi0) + (re|im), k-quad q of chunk starting at k0
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
@@ -44,25 +52,14 @@ struct AnalysisProb {
     for (int i = 0; i < 4; ++i) {
       const int l = k0 + 4 * q + i;
       float v = 0.f;
-      if (l < Lb && mi < cs.Mc && abs(m) <= l) {
+      if (l < Lb && l >= mp && mi < cs.Mc && abs(m) <= l) {
         const float f = __ldg(reinterpret_cast<const float*>(flm + (l * l + l + m)) + (r & 1));
         v = dq(Q, Lmax, mp, l, m) * f;
       }
       x[i] = v;
     }
   }
-  __device__ void b4(int mp, int n0i, int k0, int c, int q, float* x) const {
-    const int ni = n0i + c;
-    const int n = cs.n0 + cs.nstep * ni;
-    const int N = 2 * Lb - 1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int l = k0 + 4 * q + i;
-      float v = 0.f;
-      if (l < Lb && ni < cs.Nc && abs(n) <= l) v = dq(Q, Lmax, mp, l, n) * __ldg(psi + (size_t)l * N + (n + Lb - 1));
-      x[i] = v;
-    }
-  }
+  __device__ void b4(int mp, int n0i, int k0, int c, int q, float* x) const { tab4(tb, mp, n0i / BNC, k0, c, q, x); }
   // 16 accumulator columns [c0, c0+16) of row r; lanes r, r^1 hold re/im of the same m
   __device__ void store16(int mp, int mi0, int n0i, int r, int c0, const float* d) const {
     const int mi = mi0 + (r >> 1);
@@ -93,16 +90,13 @@ struct AnalysisProb {
 };
 
 struct SynthesisProb {
-  const float* Q; int Lmax; const cx<float>* Y; const float* psi; int Lb; ColSet cs; cx<float>* Z;
-  // K runs over ni with |n| <= lmax of the l-tile; no work if m' > lmax
+  const cx<float>* Y; TcTab tb; int Lb; ColSet cs; cx<float>* Z;
+  // K chunks over ni: the table's run for (m', l-tile) (empty if m' > max l of the tile)
   __device__ void tile(int& mp, int& mi0, int& l0, int& kb, int& ke) const {
     mp = blockIdx.z; mi0 = blockIdx.y * (BM / 2); l0 = blockIdx.x * BNC;
-    const int lhi = min(l0 + BNC, Lb) - 1;
-    if (mp > lhi) { kb = ke = 0; return; }
-    const int d = -lhi - cs.n0;
-    kb = d <= 0 ? 0 : (d + cs.nstep - 1) / cs.nstep;
-    const int dmax = lhi - cs.n0;
-    ke = dmax < 0 ? 0 : min(cs.Nc, dmax / cs.nstep + 1);
+    const int2 rg = tb.range[mp * tb.ntiles + blockIdx.x];
+    kb = rg.x * TC_CHUNK_K;
+    ke = (rg.x + rg.y) * TC_CHUNK_K;
   }
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
     const int mi = mi0 + (r >> 1);
@@ -118,20 +112,7 @@ struct SynthesisProb {
       x[i] = v;
     }
   }
-  __device__ void b4(int mp, int l0, int k0, int c, int q, float* x) const {
-    const int l = l0 + c;
-    const int N = 2 * Lb - 1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int ni = k0 + 4 * q + i;
-      float v = 0.f;
-      if (l < Lb && l >= mp && ni < cs.Nc) {
-        const int n = cs.n0 + cs.nstep * ni;
-        if (abs(n) <= l) v = dq(Q, Lmax, mp, l, n) * __ldg(psi + (size_t)l * N + (n + Lb - 1));
-      }
-      x[i] = v;
-    }
-  }
+  __device__ void b4(int mp, int l0, int k0, int c, int q, float* x) const { tab4(tb, mp, l0 / BNC, k0, c, q, x); }
   __device__ void store16(int mp, int mi0, int l0, int r, int c0, const float* d) const {
     const int mi = mi0 + (r >> 1);
     const bool odd = r & 1;
@@ -208,22 +189,119 @@ __global__ void __launch_bounds__(256) synth_reduce_kernel(const double* __restr
   }
 }
 
+// Table fills: block (tile, m'), thread = row of the 256-row chunks.
+__global__ void __launch_bounds__(256) fill_analysis_table_kernel(const float* __restrict__ Q, int Lmax,
+                                                                 const float* __restrict__ psi, int Lb, ColSet cs,
+                                                                 TcTab t, float* __restrict__ data) {
+  const int mp = blockIdx.y, tile = blockIdx.x, r = threadIdx.x;
+  const int2 rg = t.range[mp * t.ntiles + tile];
+  const long long base = t.base[mp * t.ntiles + tile];
+  const int ni = tile * TC_TILE_ROWS + r, n = cs.n0 + cs.nstep * ni, N = 2 * Lb - 1;
+  for (int kc = rg.x; kc < rg.x + rg.y; ++kc) {
+    float* chunk = data + (size_t)(base + kc) * TC_CHUNK_FLOATS;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int l = kc * TC_CHUNK_K + 4 * q + i;
+        v[i] = (ni < cs.Nc && l < Lb && l >= mp && abs(n) <= l)
+                   ? dq(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)]
+                   : 0.f;
+      }
+      *reinterpret_cast<float4*>(chunk + (r >> 3) * 256 + q * 32 + (r & 7) * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+}
+__global__ void __launch_bounds__(256) fill_synthesis_table_kernel(const float* __restrict__ Q, int Lmax,
+                                                                  const float* __restrict__ psi, int Lb, ColSet cs,
+                                                                  TcTab t, float* __restrict__ data) {
+  const int mp = blockIdx.y, tile = blockIdx.x, r = threadIdx.x;
+  const int2 rg = t.range[mp * t.ntiles + tile];
+  const long long base = t.base[mp * t.ntiles + tile];
+  const int l = tile * TC_TILE_ROWS + r, N = 2 * Lb - 1;
+  for (int kc = rg.x; kc < rg.x + rg.y; ++kc) {
+    float* chunk = data + (size_t)(base + kc) * TC_CHUNK_FLOATS;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int ni = kc * TC_CHUNK_K + 4 * q + i, n = cs.n0 + cs.nstep * ni;
+        v[i] = (l < Lb && l >= mp && ni < cs.Nc && abs(n) <= l)
+                   ? dq(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)]
+                   : 0.f;
+      }
+      *reinterpret_cast<float4*>(chunk + (r >> 3) * 256 + q * 32 + (r & 7) * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
 // Host entry points used by crv.cu
 // ---------------------------------------------------------------------------
-bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, const float* psi, int Lb, ColSet cs,
-                 cx<float>* X, int* err, cudaStream_t st) {
-  tc::AnalysisProb pb{Q32, Lmax, flm, psi, Lb, cs, X};
-  dim3 grid((cs.Nc + tc::BNC - 1) / tc::BNC, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
+void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
+  ntiles = (cs.Nc + TC_TILE_ROWS - 1) / TC_TILE_ROWS;
+  const int nchunk = (Lb + TC_CHUNK_K - 1) / TC_CHUNK_K;
+  range.assign((size_t)Lb * ntiles, make_int2(0, 0));
+  for (int mp = 0; mp < Lb; ++mp)
+    for (int t = 0; t < ntiles; ++t) {
+      const int nlo = cs.n0 + cs.nstep * (t * TC_TILE_ROWS);
+      const int nhi = cs.n0 + cs.nstep * (std::min((t + 1) * TC_TILE_ROWS, cs.Nc) - 1);
+      const int bmin = (nlo <= 0 && nhi >= 0) ? 0 : std::min(std::abs(nlo), std::abs(nhi));
+      const int kb = std::max(mp, bmin);
+      if (kb >= Lb) continue;
+      range[(size_t)mp * ntiles + t] = make_int2(kb / TC_CHUNK_K, nchunk - kb / TC_CHUNK_K);
+    }
+}
+
+void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
+  ntiles = (Lb + TC_TILE_ROWS - 1) / TC_TILE_ROWS;
+  range.assign((size_t)Lb * ntiles, make_int2(0, 0));
+  for (int mp = 0; mp < Lb; ++mp)
+    for (int t = 0; t < ntiles; ++t) {
+      const int lhi = std::min((t + 1) * TC_TILE_ROWS, Lb) - 1;
+      if (mp > lhi) continue;
+      const int d = -lhi - cs.n0, dmax = lhi - cs.n0;
+      const int kb = d <= 0 ? 0 : (d + cs.nstep - 1) / cs.nstep;
+      const int ke = dmax < 0 ? 0 : std::min(cs.Nc, dmax / cs.nstep + 1);
+      if (ke <= kb) continue;
+      const int c0 = kb / TC_CHUNK_K, c1 = (ke + TC_CHUNK_K - 1) / TC_CHUNK_K;
+      range[(size_t)mp * ntiles + t] = make_int2(c0, c1 - c0);
+    }
+}
+
+bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
+                            cudaStream_t st) {
+  dim3 g(t.ntiles, Lb);
+  KTimer kt(K_MISC, st);
+  tc::fill_analysis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, data);
+  kt.done();
+  return launch_ok("fill_analysis_table_kernel");
+}
+
+bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
+                             cudaStream_t st) {
+  dim3 g(t.ntiles, Lb);
+  KTimer kt(K_MISC, st);
+  tc::fill_synthesis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, data);
+  kt.done();
+  return launch_ok("fill_synthesis_table_kernel");
+}
+
+bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
+                 int* err, cudaStream_t st) {
+  tc::AnalysisProb pb{Q32, Lmax, flm, tb, Lb, cs, X};
+  dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
   return launch_tc_gemm<tc::AnalysisProb, tc::BNC>(pb, grid, err, st, K_TC_A);
 }
 
-bool tc_synthesis(const float* Q32, const double* Q64, int Lmax, const cx<float>* Y, const float* psi, int Lb,
-                  ColSet cs, cx<float>* Zscratch, cx<double>* flm, int* err, cudaStream_t st) {
-  tc::SynthesisProb pb{Q32, Lmax, Y, psi, Lb, cs, Zscratch};
-  dim3 grid((Lb + tc::BNC - 1) / tc::BNC, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
+bool tc_synthesis(const double* Q64, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
+                  cx<double>* flm, int* err, cudaStream_t st) {
+  tc::SynthesisProb pb{Y, tb, Lb, cs, Zscratch};
+  dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
   if (!launch_tc_gemm<tc::SynthesisProb, tc::BNC>(pb, grid, err, st, K_TC_S)) return false;
   dim3 g2((Lb + 31) / 32, (cs.Mc + 31) / 32);
   KTimer kt(K_TC_S, st);

@@ -40,8 +40,9 @@ struct ColSet {
 // ---------------------------------------------------------------------------
 template <class St> struct Mirror { static constexpr bool value = false; };
 
-template <class T, int NT, bool COLS>
-__device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned char* smraw, int P) {
+template <class T, int NT, bool COLS, int PT>
+__device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned char* smraw, int Prt) {
+  const int P = PT ? PT : Prt;
   const int TP = P >> 4, G = NT / TP, XL = xlen(P);
   cx<T>* sm = reinterpret_cast<cx<T>*>(smraw);
   if (COLS) { g = threadIdx.x % G; t = threadIdx.x / G; }
@@ -55,15 +56,23 @@ __device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned
 // Blocks of NT threads; FP32 blocks of 256 threads fit twice on an SM (<= 128 registers).
 template <class T, int NT> struct FftMinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1; };
 
-template <class T, int NT, bool COLS, class Ld, class St>
+// PT: P as a compile-time constant, or 0 (from the table). SPAN: each block takes one
+// contiguous run of sequences (neighbouring columns then share sectors through L1), else
+// blocks stride through the sequences together (neighbouring blocks fill each sector of
+// a large output at about the same time).
+template <class T, int NT, bool COLS, int PT, bool SPAN, class Ld, class St>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(DftTab<T> tb, int sign, int nseq, Ld ld, St st) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = tb.N, TP = tb.P >> 4, G = NT / TP;
+  const int N = tb.N, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
   int g, t;
   XBuf2<T> buf;
-  fft_slot<T, NT, COLS>(g, t, buf, smraw, tb.P);
+  fft_slot<T, NT, COLS, PT>(g, t, buf, smraw, tb.P);
   const cx<T>* __restrict__ kh = (sign < 0) ? tb.khat_f : tb.khat_i;
-  for (int s0 = blockIdx.x * G; s0 < nseq; s0 += gridDim.x * G) {
+  const int span = SPAN ? (nseq + gridDim.x * G - 1) / (gridDim.x * G) * G : G;
+  const int s_beg = SPAN ? blockIdx.x * span : blockIdx.x * G;
+  const int s_end = SPAN ? min(nseq, (blockIdx.x + 1) * span) : nseq;
+  const int s_step = SPAN ? G : gridDim.x * G;
+  for (int s0 = s_beg; s0 < s_end; s0 += s_step) {
     const int c = s0 + g;
     const bool valid = c < nseq;
     cx<T> v[16];
@@ -73,10 +82,10 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
       v[q] = mk<T>(0, 0);
       if (q < 8 && valid && j < N) v[q] = ld(c, j) * chirp_of(tb, j, sign);
     }
-    fft16<-1, true>(v, tb, buf, t);
+    fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] * kh[t + q * TP];
-    fft16<+1, false>(v, tb, buf, t);
+    fft16<+1, false, PT>(v, tb, buf, t);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int k = t + q * TP;
@@ -327,18 +336,20 @@ struct StMapRow {
 // scale * i^{m*pa + n*pb + pc}. In: Xb[b][c] (b < Lb); out: Y[m'][c] (m' < Lb).
 // Threads laid out as in dft_kernel with COLS = true.
 // ---------------------------------------------------------------------------
-template <class T, int NT>
+template <class T, int NT, int PT>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int Lb,
                                                                     const cx<T>* __restrict__ Xb,
                                                                     cx<T>* __restrict__ Y, ColSet cs, T scale, int pa,
                                                                     int pb, int pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int N = tb.N, Q = ct.Q, TP = tb.P >> 4, G = NT / TP;
+  const int N = tb.N, Q = PT ? PT : ct.Q, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
   int g, t;
   XBuf2<T> buf;
-  fft_slot<T, NT, true>(g, t, buf, smraw, tb.P);
+  fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
   const T invN = (T)1 / (T)N;
-  for (int s0 = blockIdx.x * G; s0 < ncols; s0 += gridDim.x * G) {
+  const int span = (ncols + gridDim.x * G - 1) / (gridDim.x * G) * G;
+  const int s_end = min(ncols, (blockIdx.x + 1) * span);
+  for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
     const int c = s0 + g;
     const bool valid = c < ncols;
     const int par = valid ? cs.par(c) : 0;
@@ -354,10 +365,10 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
         v[q] = x * chirp_of(tb, j, -1);
       }
     }
-    fft16<-1, true>(v, tb, buf, t);
+    fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] * tb.khat_f[t + q * TP];
-    fft16<+1, false>(v, tb, buf, t);
+    fft16<+1, false, PT>(v, tb, buf, t);
     // u_{m''} at index m'' mod Q: D_{m'' mod N} h_k e^{-i m'' pi/N} / N; zero for Lb <= index <= Q - Lb
     {
       const XBuf<T> x = buf.take();
@@ -371,10 +382,10 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
 #pragma unroll
       for (int q = 0; q < 16; ++q) v[q] = x[t + q * TP];
     }
-    fft16<-1, false>(v, tb, buf, t);
+    fft16<-1, false, PT>(v, tb, buf, t);
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] * ct.what[t + q * TP];
-    fft16<+1, false>(v, tb, buf, t);
+    fft16<+1, false, PT>(v, tb, buf, t);
     // fold Yhat_{m'} = Y_{m'} + (-1)^{par} Y_{-m'}, phase and scale
     const XBuf<T> y = buf.take();
 #pragma unroll
