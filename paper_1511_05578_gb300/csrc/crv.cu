@@ -321,14 +321,12 @@ static int build_fft(crv_plan_s* p, int Lb) {
   host_fft(ki, -1);
   for (auto& v : kf) v /= (double)P;
   for (auto& v : ki) v /= (double)P;
-  // v[t] = w(-t), t in [-(2Lb-2), 2Lb-2]; w(p) = int_0^pi sin(b) e^{i p b} db
+  // v[t] = w_e(-t) = w_e(t), t in [-(2Lb-2), 2Lb-2]: the even part of the weights
+  // w(p) = int_0^pi sin(b) e^{i p b} db, i.e. 2 / (1 - p^2) for even p and 0 for odd p (the
+  // odd part, +-i pi/2 at p = +-1, cancels in the folded quadrature)
   for (int t = -(2 * Lb - 2); t <= 2 * Lb - 2; ++t) {
     const int pp = -t;
-    std::complex<double> w;
-    if (pp % 2 == 0) w = 2.0 / (1.0 - (double)pp * pp);
-    else if (pp == 1) w = std::complex<double>(0, M_PI / 2);
-    else if (pp == -1) w = std::complex<double>(0, -M_PI / 2);
-    else w = 0.0;
+    const double w = (pp % 2 == 0) ? 2.0 / (1.0 - (double)pp * pp) : 0.0;
     wv[((t % Q) + Q) % Q] = w;
   }
   host_fft(wv, -1);
@@ -446,7 +444,8 @@ static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, 
   const size_t smem = fft_smem_bytes<T>(NT);
   if (!set_smem(beta_quad_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
-  const int grid = std::max(1, std::min((ncols + G - 1) / G, num_sms() * bps));
+  const int npair = num_col_pairs(cs);
+  const int grid = std::max(1, std::min((npair + G - 1) / G, num_sms() * bps));
   KTimer kt(K_BETA_QUAD, s);
   beta_quad_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc);
   kt.done();
@@ -501,9 +500,9 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
-  LdBetaSynth<double> lb{p->wG, Mc, Ls, N, cs, fs.d.hphase};
-  StRows<double> sr{p->wF, Mc, Ls};
-  if (!run_cols<double>(K_BETA_SYNTH, fs.d, +1, Mc, lb, sr, st)) return false;
+  LdBetaSynthPair<double> lb{p->wG, Mc, Ls, N, cs, fs.d.hphase};
+  StRowsPair<double> sr{p->wF, Mc, Ls, cs};
+  if (!run_cols<double>(K_BETA_SYNTH, fs.d, +1, num_col_pairs(cs), lb, sr, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
   StMapRow sm{map, N, real};
   return run_rows<double>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
@@ -548,8 +547,9 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols_wide<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, ncols, LdBetaSynth<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase},
-                         StRows<T>{Xb, ncols, Lb}, st))
+  if (!run_cols_wide<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, num_col_pairs(cs),
+                        LdBetaSynthPair<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase}, StRowsPair<T>{Xb, ncols, Lb, cs},
+                        st))
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);

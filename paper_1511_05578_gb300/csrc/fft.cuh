@@ -34,10 +34,11 @@ struct DftTab {
 };
 
 // Weight spectrum for the correlation of Eq. gmnmp (same P as the DftTab of the length).
+// Only the even part w_e of the weights enters (see beta_quad_kernel).
 template <class T>
 struct CorrTab {
   int Q = 0;
-  const cx<T>* what = nullptr;  // [Q] FFT_Q(v)/Q, v[t] = w(-t), t in (-(2L-1), 2L-1) wrapped
+  const cx<T>* what = nullptr;  // [Q] FFT_Q(v)/Q, v[t] = w_e(t) = w_e(-t), |t| < 2L-1, wrapped
 };
 
 

@@ -35,10 +35,11 @@ struct ColSet {
 // COLS = true (columns): consecutive sequences are adjacent in memory; the G
 //   transforms of a block interleave their threads (g fastest), so each load or
 //   store touches G adjacent sequences, and the exchange buffers interleave too.
-// Storers get st(c, k, X_k, X_{(N-k) mod N}) for every k < N; the second value (the
-// real-pair unpacking) is gathered only for storers that declare kMirror.
+// Storers get st(c, k, X_k, X_k') for every k < N, where k' is set by Mirror<St>:
+// 0: no partner (X_k' = X_k), 1: k' = (N - k) mod N (real-pair unpacking), 2: k' = N - 1 - k
+// (beta-reflection pairs); the partner is gathered through shared memory.
 // ---------------------------------------------------------------------------
-template <class St> struct Mirror { static constexpr bool value = false; };
+template <class St> struct Mirror { static constexpr int value = 0; };
 
 template <class T, int NT, bool COLS, int PT>
 __device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned char* smraw, int Prt) {
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
       const int k = t + q * TP;
       v[q] = v[q] * chirp_of(tb, k < N ? k : 0, sign);
     }
-    if constexpr (Mirror<St>::value) {
+    if constexpr (Mirror<St>::value != 0) {
       const XBuf<T> x = buf.take();
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -102,7 +103,8 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int k = t + q * TP;
-        if (valid && k < N) st(c, k, v[q], x[k == 0 ? 0 : N - k]);
+        const int kp = Mirror<St>::value == 1 ? (k == 0 ? 0 : N - k) : N - 1 - k;
+        if (valid && k < N) st(c, k, v[q], x[kp]);
       }
     } else {
 #pragma unroll
@@ -118,25 +120,53 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
 // Loaders / storers
 // ---------------------------------------------------------------------------
 
-// Synthesis over beta of a folded column X[m'][c], m' = 0..K-1 (row stride C):
-// z_{m' mod N} = X~_{m'} e^{i m' pi/N}, X~_{-m'} = (-1)^{m+n+extra} X~_{m'}.
+// Column pairs. Columns c_A = (2 i, ni) and c_B = (2 i + 1, ni) (m and m + 1, one n) have
+// opposite parities of m + n + extra, so one of their beta extensions is symmetric under
+// b -> N-1-b (m' -> -m') and the other antisymmetric: one DFT of the sum serves both and
+// the halves separate by that reflection. Pair index p = i * Nc + ni; c_B = -1 if 2i+1 = Mc.
+struct ColPair {
+  int cA, cB, parA;  // parA = parity of m + n + extra of column A (B has the other)
+};
+__device__ __forceinline__ ColPair col_pair(const ColSet& cs, int p) {
+  const int i = (int)cs.fNc.div((uint32_t)p), ni = p - i * cs.Nc;
+  ColPair r;
+  r.cA = 2 * i * cs.Nc + ni;
+  r.cB = (2 * i + 1 < cs.Mc) ? r.cA + cs.Nc : -1;
+  r.parA = (cs.m0 + cs.n0 + cs.nstep * ni + cs.extra) & 1;
+  return r;
+}
+__host__ __device__ inline int num_col_pairs(const ColSet& cs) { return (cs.Mc + 1) / 2 * cs.Nc; }
+
+// Synthesis over beta of a column pair: z_j = (X~A + X~B)_{m'} e^{i m' pi/N}.
 template <class T>
-struct LdBetaSynth {
+struct LdBetaSynthPair {
   const cx<T>* X; int C, K, N; ColSet cs; const cx<T>* hphase;
-  __device__ cx<T> operator()(int c, int j) const {
-    int mp = (j < K) ? j : j - N;
-    int a = mp < 0 ? -mp : mp;
-    cx<T> v = X[(size_t)a * C + c];
-    if (mp < 0 && cs.par(c)) v = mk(-v.re, -v.im);
+  __device__ cx<T> operator()(int p, int j) const {
+    const ColPair cp = col_pair(cs, p);
+    const int mp = (j < K) ? j : j - N;
+    const int a = mp < 0 ? -mp : mp;
+    cx<T> v = X[(size_t)a * C + cp.cA];
+    if (mp < 0 && cp.parA) v = mk(-v.re, -v.im);
+    if (cp.cB >= 0) {
+      const cx<T> w = X[(size_t)a * C + cp.cB];
+      v = (mp < 0 && !cp.parA) ? v - w : v + w;
+    }
     return v * hphase[j];
   }
 };
-// keep k < Kout, Y[k][c]
+// F_A, F_B = (F_b +- F_{N-1-b}) / 2 (the symmetric half to the even-parity column), b < Kout.
 template <class T>
-struct StRows {
-  cx<T>* Y; int C, Kout;
-  __device__ void operator()(int c, int k, cx<T> v, cx<T>) const { if (k < Kout) Y[(size_t)k * C + c] = v; }
+struct StRowsPair {
+  cx<T>* Y; int C, Kout; ColSet cs;
+  __device__ void operator()(int p, int k, cx<T> v, cx<T> vr) const {
+    if (k >= Kout) return;
+    const ColPair cp = col_pair(cs, p);
+    const cx<T> sym = (v + vr) * (T)0.5, anti = (v - vr) * (T)0.5;
+    Y[(size_t)k * C + cp.cA] = cp.parA ? anti : sym;
+    if (cp.cB >= 0) Y[(size_t)k * C + cp.cB] = cp.parA ? sym : anti;
+  }
 };
+template <class T> struct Mirror<StRowsPair<T>> { static constexpr int value = 2; };
 
 // Ring inverse, step over n: row (b, mi) of Xb (Nc contiguous) -> T[b][mi][g].
 template <class T>
@@ -256,7 +286,7 @@ struct StRingNPair {
     if (2 * c + 1 < nrows) U[(size_t)(2 * c + 1) * Nc + ni] = b;
   }
 };
-template <class T> struct Mirror<StRingNPair<T>> { static constexpr bool value = true; };
+template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 1; };
 // Inverse over m with Hermitian input and real output: columns g = 2c, 2c+1 packed.
 template <class T>
 struct LdRingMPair {
@@ -328,13 +358,18 @@ struct StMapRow {
 };
 
 // ---------------------------------------------------------------------------
-// Exact quadrature over beta (Eqs. TildaFmn, Fmnmp, gmnmp), folded onto m' >= 0:
-// per column c: extend the Lb ring values to 2Lb-1 with (-1)^{m+n+extra}, DFT
-// (sign -1, half-sample phase e^{-i m'' pi/N}/N), correlate with the weights w
-// (precomputed transform of v[t] = w(-t) on Q = P points), fold
-// Yhat_{m'} = Y_{m'} + (-1)^{m+n+extra} Y_{-m'} (m' > 0), and multiply by
-// scale * i^{m*pa + n*pb + pc}. In: Xb[b][c] (b < Lb); out: Y[m'][c] (m' < Lb).
-// Threads laid out as in dft_kernel with COLS = true.
+// Exact quadrature over beta (Eqs. TildaFmn, Fmnmp, gmnmp), folded onto m' >= 0, for a
+// column pair (ColPair): extend the Lb ring values of each column to 2Lb-1 with
+// (-1)^{m+n+extra} and add the two, DFT (sign -1, half-sample phase e^{-i m'' pi/N}/N),
+// correlate with the even part w_e of the weights (precomputed transform of
+// v[t] = w_e(t) on Q = P points), and unfold: with Yt = D * w_e,
+//   Yhat_sym(m') = Yt(m') + Yt(-m')  (m' > 0; Yt(0) at m' = 0),
+//   Yhat_anti(m') = Yt(m') - Yt(-m') (m' > 0; 0 at m' = 0),
+// the symmetric one for the column of even parity; then scale * i^{m pa + n pb + pc}.
+// This equals the fold Y(m') + (-1)^{m+n+extra} Y(-m') of the full-weight correlation of
+// each column: the odd weights (p = +-1) cancel in that fold, and the even (odd) part of
+// the DFT of a symmetric (antisymmetric) extension is all of it.
+// In: Xb[b][c] (b < Lb); out: Y[m'][c] (m' < Lb). Threads as in dft_kernel with COLS.
 // ---------------------------------------------------------------------------
 template <class T, int NT, int PT>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int Lb,
@@ -343,25 +378,31 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
                                                                     int pb, int pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, Q = PT ? PT : ct.Q, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
+  const int npair = num_col_pairs(cs);
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
   const T invN = (T)1 / (T)N;
-  const int span = (ncols + gridDim.x * G - 1) / (gridDim.x * G) * G;
-  const int s_end = min(ncols, (blockIdx.x + 1) * span);
+  const int span = (npair + gridDim.x * G - 1) / (gridDim.x * G) * G;
+  const int s_end = min(npair, (blockIdx.x + 1) * span);
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
-    const int c = s0 + g;
-    const bool valid = c < ncols;
-    const int par = valid ? cs.par(c) : 0;
-    // extension to the 2Lb-1 nodes of the full circle, then the chirp
+    const int p = s0 + g;
+    const bool valid = p < s_end;
+    const ColPair cp = valid ? col_pair(cs, p) : ColPair{0, -1, 0};
+    // extensions to the 2Lb-1 nodes of the full circle, summed, then the chirp
     cx<T> v[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int j = t + q * TP;
       v[q] = mk<T>(0, 0);
       if (q < 8 && valid && j < N) {
-        cx<T> x = Xb[(size_t)(j < Lb ? j : N - 1 - j) * ncols + c];
-        if (j >= Lb && par) x = mk(-x.re, -x.im);
+        const size_t row = (size_t)(j < Lb ? j : N - 1 - j) * ncols;
+        cx<T> x = Xb[row + cp.cA];
+        if (j >= Lb && cp.parA) x = mk(-x.re, -x.im);
+        if (cp.cB >= 0) {
+          const cx<T> y = Xb[row + cp.cB];
+          x = (j >= Lb && !cp.parA) ? x - y : x + y;
+        }
         v[q] = x * chirp_of(tb, j, -1);
       }
     }
@@ -386,7 +427,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
 #pragma unroll
     for (int q = 0; q < 16; ++q) v[q] = v[q] * ct.what[t + q * TP];
     fft16<+1, false, PT>(v, tb, buf, t);
-    // fold Yhat_{m'} = Y_{m'} + (-1)^{par} Y_{-m'}, phase and scale
+    // unfold into the two columns
     const XBuf<T> y = buf.take();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -395,18 +436,20 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     }
     __syncthreads();
     if (valid) {
-      const int m = cs.m_of(c), n = cs.n_of(c);
-      const int ph = imod(m * pa + n * pb + pc, 4);
+      const int mA = cs.m_of(cp.cA), n = cs.n_of(cp.cA);
+      const int phA = imod(mA * pa + n * pb + pc, 4), phB = imod((mA + 1) * pa + n * pb + pc, 4);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int mp = t + q * TP;
         if (mp < Lb) {
-          cx<T> val = v[q];
+          cx<T> sym = v[q], anti = mk<T>(0, 0);
           if (mp > 0) {
             const cx<T> w = y[Q - mp];
-            val = par ? val - w : val + w;
+            anti = sym - w;
+            sym = sym + w;
           }
-          Y[(size_t)mp * ncols + c] = mul_ipow(val * scale, ph);
+          Y[(size_t)mp * ncols + cp.cA] = mul_ipow((cp.parA ? anti : sym) * scale, phA);
+          if (cp.cB >= 0) Y[(size_t)mp * ncols + cp.cB] = mul_ipow((cp.parA ? sym : anti) * scale, phB);
         }
       }
     }
