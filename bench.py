@@ -155,18 +155,18 @@ def kind_work(L, lam, J0, el_bytes, w_bytes):
         w[k] = (B0 + b, F0 + f)
     for (j, Lb, N, Mc, Nc) in shapes:
         vol = Lb * Mc * Nc * el_bytes           # X, Xb, Y volumes (complex)
-        ring_t = Lb * Mc * N * el_bytes         # T after the n -> gamma step
-        ring_u = Lb * N * Nc * el_bytes         # U after the gamma -> n step
         wv = Lb * N * N * w_bytes               # W_j
         terms = contraction_terms(Lb)
         Q = 1 << max(3, (4 * Lb - 4).bit_length())
         add("contract_analysis", vol, 4.0 * terms)
         add("tc_analysis", vol, 4.0 * terms)
+        Nh = (Nc + 1) // 2                      # columns n >= 0 (real signals: F_{-m,-n} = conj F_{m,n})
+        ring_h = Lb * N * Nh * el_bytes         # ring buffer [b][a][h]
         add("beta_synth", 2 * vol, Mc * Nc * fft_flops(N))
-        add("ring_inv_n", vol + ring_t, Lb * Mc * fft_flops(N))
-        add("ring_inv_m", ring_t + wv, Lb * N * 0.5 * fft_flops(N))
-        add("ring_fwd_g", wv + ring_u, Lb * N * 0.5 * fft_flops(N))
-        add("ring_fwd_a", ring_u + vol, Lb * Nc * fft_flops(N))
+        add("ring_inv_m", vol + ring_h, Lb * Nh * fft_flops(N))
+        add("ring_inv_n", ring_h + wv, Lb * N * 0.5 * fft_flops(N))
+        add("ring_fwd_g", wv + ring_h, Lb * N * 0.5 * fft_flops(N))
+        add("ring_fwd_a", ring_h + vol, Lb * Nh * fft_flops(N))
         add("beta_quad", 2 * vol, Mc * Nc * (fft_flops(N) + 2 * fft_flops(Q) + 6 * Q))
         add("contract_synthesis", vol, 4.0 * terms)
         add("tc_synthesis", vol, 4.0 * terms)

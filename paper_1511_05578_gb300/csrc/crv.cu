@@ -518,9 +518,10 @@ template <class T> static const T* psi_of(crv_plan_s* p, int j);
 template <> const double* psi_of<double>(crv_plan_s* p, int j) { return p->dpsi[j]; }
 template <> const float* psi_of<float>(crv_plan_s* p, int j) { return p->dpsi32[j]; }
 
+// Rings per chunk of the ring buffer (rows padded to N + 1 elements in the analysis).
 static int ring_chunk(crv_plan_s* p, int Lb, size_t elem) {
   const int N = 2 * Lb - 1;
-  const size_t per = (size_t)N * std::max(p->mc(Lb), p->nc(Lb)) * elem;
+  const size_t per = (size_t)(N + 1) * std::max(p->mc(Lb), p->nc(Lb)) * elem;
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lb, p->ring_bytes / per));
 }
 
@@ -553,18 +554,23 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
+  const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
-    LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
-    StContig<T> sc{R, N};
-    if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
-    if (p->real) {  // Hermitian columns in pairs: real output in re and im
+    if (p->real) {
+      // m step on the n >= 0 columns, then the n step with real output, rows in pairs
+      LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.Nc, ni0, N, Nh, FastDiv((uint32_t)Nh)};
+      StRingMHalf<T> sm{R, N, Nh, FastDiv((uint32_t)Nh)};
+      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nh, lm, sm, st)) return false;
       const int npair = (N + 1) / 2;
-      LdRingMPair<T> lm{R, cs.Mc, N, npair, FastDiv((uint32_t)npair)};
-      StWPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
-      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * npair, lm, sw, st)) return false;
+      LdRingNHerm<T> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair)};
+      StWRowPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
+      if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * npair, ln, sw, st)) return false;
     } else {
-      LdRingM<T> lm{R, cs.Mc, cs.m0, N, false, FastDiv((uint32_t)N)};
+      LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
+      StContig<T> sc{R, N + 1};
+      if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
+      LdRingM<T> lm{R, cs.Mc, cs.m0, N, N + 1, false, FastDiv((uint32_t)N)};
       StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false, FastDiv((uint32_t)N)};
       if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
     }
@@ -582,21 +588,28 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   cx<T>* R = (cx<T>*)p->wR;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
+  const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
-    if (p->real) {  // real rows in pairs
+    if (p->real) {
+      // g step on real rows in pairs keeping n >= 0, then the a step on those columns,
+      // which also fills the n < 0 columns by conjugation
       const int nrows = nr * N;
       LdWRowPair<T, InT> lw{W + (size_t)b0 * wstride, N, nrows};
-      StRingNPair<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, nrows, (T)1 / (T)N};
+      StRingNPairHalf<T> sn{R, Nh, cs.nstep, N, nrows, (T)1 / (T)N};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, (nrows + 1) / 2, lw, sn, st)) return false;
+      LdRingAHalf<T> la{R, N, Nh, FastDiv((uint32_t)Nh)};
+      StRingAHalf<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.Nc, ni0, N, Nh, (T)1 / (T)N,
+                        FastDiv((uint32_t)Nh)};
+      if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * Nh, la, sa, st)) return false;
     } else {
       LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, false};
       StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
+      LdRingA<T> la{R, cs.Nc, N, FastDiv((uint32_t)cs.Nc)};
+      StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N, FastDiv((uint32_t)cs.Nc)};
+      if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
     }
-    LdRingA<T> la{R, cs.Nc, N, FastDiv((uint32_t)cs.Nc)};
-    StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N, FastDiv((uint32_t)cs.Nc)};
-    if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
@@ -866,7 +879,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (stt == CRV_OK) cudaMemset(p->d_err, 0, sizeof(int));
   {
     // ring-chunk buffer: at least one ring, at most all rings, about 96 MB (L2-resident)
-    const size_t one = (size_t)N * std::max(Mc, Nc) * el;
+    const size_t one = (size_t)(N + 1) * std::max(Mc, Nc) * el;
     p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)96 << 20));
   }
   p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);

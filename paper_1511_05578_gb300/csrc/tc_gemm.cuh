@@ -1,13 +1,13 @@
-// tcgen05 split-FP32 GEMM engine (sm_103a), shared by the Delta contractions and the
-// prime-factor DFTs of the mixed path.
+// tcgen05 split-FP32 GEMM engine (sm_103a) of the Delta contractions of the mixed path.
 //
 // D[128 x BN] = sum_k A[128 x k] B[BN x k]^T with FP32 operands produced on the fly by a
 // problem object. Each operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a
 // K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM accumulator (split-FP32,
 // ~2^-22 per product). All 512 threads build the operand stage in shared memory in the
-// canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered;
-// one thread issues tcgen05.mma and commits to the stage's mbarrier; waits are bounded
-// and set an error flag instead of hanging; four warps drain TMEM with tcgen05.ld.
+// canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered,
+// with the next chunk's loads in flight; one thread issues tcgen05.mma and commits to the
+// stage's mbarrier; waits are bounded and set an error flag instead of hanging; all
+// warps drain TMEM with tcgen05.ld.
 #pragma once
 #include <cstdint>
 
@@ -156,37 +156,40 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(Prob pb, int* err) {
   const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
+  // Operand quads of one K chunk per thread: A 128 rows x 8 k-quads, B BN rows x 8 k-quads.
+  // The loads of chunk c + 1 are issued as soon as chunk c is in shared memory, so their
+  // latency overlaps the barrier and the MMAs of chunk c.
+  constexpr int NA = BM * (BK / 4) / NT, NB = BN * (BK / 4) / NT;
+  float xa[NA][4], xb[NB][4];
+  auto load_chunk = [&](int c) {
+    const int k0 = kb + c * BK;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int it = tid + i * NT;
+      pb.a4(mp, r0, k0, it % BM, it / BM, xa[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int it = tid + i * NT;
+      pb.b4(mp, c0g, k0, it % BN, it / BN, xb[i]);
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % STAGES;
     if (c >= STAGES) ok = mbar_wait(&bars[s], (uint32_t)((c / STAGES) - 1) & 1u, err) && ok;
     unsigned char* st = base + s * STAGE_BYTES;
-    const int k0 = kb + c * BK;
-    // A: 128 rows x 8 k-quads, B: 256 rows x 8 k-quads; 2 + 4 chunks per thread.
-    // All loads of a thread are issued before any split/store (latency hiding).
-    {
-      constexpr int NA = BM * (BK / 4) / NT, NB = BN * (BK / 4) / NT;
-      float xa[NA][4], xb[NB][4];
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int it = tid + i * NT;
-        pb.a4(mp, r0, k0, it % BM, it / BM, xa[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        const int it = tid + i * NT;
-        pb.b4(mp, c0g, k0, it % BN, it / BN, xb[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int it = tid + i * NT;
-        put4(st, st + A_BYTES, it % BM, it / BM, xa[i]);
-      }
-#pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        const int it = tid + i * NT;
-        put4(st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, it % BN, it / BN, xb[i]);
-      }
+    for (int i = 0; i < NA; ++i) {
+      const int it = tid + i * NT;
+      put4(st, st + A_BYTES, it % BM, it / BM, xa[i]);
     }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int it = tid + i * NT;
+      put4(st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, it % BN, it / BN, xb[i]);
+    }
+    if (c + 1 < nchunks) load_chunk(c + 1);
     fence_proxy_async();
     __syncthreads();
     if (tid == 0 && ok) {
@@ -210,12 +213,16 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(Prob pb, int* err) {
     ok = mbar_wait(&bars[last % STAGES], (uint32_t)(last / STAGES) & 1u, err) && ok;
   }
   fence_after();
-  if (warp < 4) {
-    const int r = warp * 32 + (tid & 31);
-    for (int cc = 0; cc < BN; cc += 16) {
+  // Epilogue on all warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lanes it may
+  // access) and the w / 4-th quarter of the BN columns.
+  {
+    constexpr int QCOLS = BN / (NT / 128);
+    const int r = (warp & 3) * 32 + (tid & 31);
+    const int cbeg = (warp >> 2) * QCOLS;
+    for (int cc = cbeg; cc < cbeg + QCOLS; cc += 16) {
       if (nchunks > 0 && ok) {
         float d[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, d);
+        tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cc, d);
         pb.store16(mp, r0, c0g, r, cc, d);
       } else {
         pb.zero16(mp, r0, c0g, r, cc);

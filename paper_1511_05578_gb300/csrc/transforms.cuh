@@ -183,27 +183,27 @@ struct LdRingN {
   }
 };
 template <class T>
-struct StContig {  // out[c][k], k < N
-  cx<T>* out; int N;
-  __device__ void operator()(int c, int k, cx<T> v, cx<T>) const { out[(size_t)c * N + k] = v; }
+struct StContig {  // out[c][k], k < N, rows of S elements
+  cx<T>* out; int S;
+  __device__ void operator()(int c, int k, cx<T> v, cx<T>) const { out[(size_t)c * S + k] = v; }
 };
 
 // Ring inverse, step over m: column (b, g) of T[b][mi][g] -> W[b][a][g].
 // real: Hermitian completion z_{N-m} = conj(z_m), output real part.
 template <class T>
-struct LdRingM {
-  const cx<T>* Tb; int Mc, m0, N; bool real; FastDiv fN;
+struct LdRingM {  // T[b][mi][g], rows of S >= N elements
+  const cx<T>* Tb; int Mc, m0, N, S; bool real; FastDiv fN;
   __device__ cx<T> operator()(int c, int j) const {
     const int b = (int)fN.div(c), g = c - b * N;
-    const cx<T>* base = Tb + (size_t)b * Mc * N + g;
+    const cx<T>* base = Tb + (size_t)b * Mc * S + g;
     int m = (j <= (N - 1) / 2) ? j : j - N;
     if (real) {
-      if (m >= 0) return base[(size_t)m * N];
-      return conj(base[(size_t)(-m) * N]);
+      if (m >= 0) return base[(size_t)m * S];
+      return conj(base[(size_t)(-m) * S]);
     }
     int mi = m - m0;
     if (mi < 0 || mi >= Mc) return mk<T>(0, 0);
-    return base[(size_t)mi * N];
+    return base[(size_t)mi * S];
   }
 };
 template <class T, class OutT>
@@ -287,31 +287,98 @@ struct StRingNPair {
   }
 };
 template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 1; };
-// Inverse over m with Hermitian input and real output: columns g = 2c, 2c+1 packed.
+// ---------------------------------------------------------------------------
+// Ring transforms of real signals. Only m >= 0 is kept (all n), and F_{-m,-n} =
+// conj F_{m,n}, so each direction needs the columns n >= 0 only: h = n / nstep < Nh,
+// column ni = ni0 + h of the n-set, whose mirror column Nc - 1 - ni holds -n (the n-set
+// is symmetric). Ring buffers are laid out [b][a][h].
+// ---------------------------------------------------------------------------
+// Analysis, step over m (sign +1) for n >= 0: column (b, h) of Xb[b][mi][ni], extended to
+// m < 0 by the conjugate of the -n column -> R[b][a][h].
 template <class T>
-struct LdRingMPair {
-  const cx<T>* Tb; int Mc, N, npair; FastDiv fP;
+struct LdRingMHalf {
+  const cx<T>* Xb; int Mc, Nc, ni0, N, Nh; FastDiv fNh;
   __device__ cx<T> operator()(int c, int j) const {
-    const int b = (int)fP.div(c), gp = c - b * npair, g1 = 2 * gp, g2 = g1 + 1;
-    const cx<T>* base = Tb + (size_t)b * Mc * N;
-    int m = (j <= (N - 1) / 2) ? j : j - N;
-    const int am = m < 0 ? -m : m;
-    cx<T> t1 = base[(size_t)am * N + g1];
-    cx<T> t2 = (g2 < N) ? base[(size_t)am * N + g2] : mk<T>(0, 0);
-    if (m < 0) { t1 = conj(t1); t2 = conj(t2); }
-    return mk<T>(t1.re - t2.im, t1.im + t2.re);
+    const int b = (int)fNh.div((uint32_t)c), ni = ni0 + (c - b * Nh);
+    const int m = (j <= (N - 1) / 2) ? j : j - N;
+    const cx<T>* base = Xb + (size_t)b * Mc * Nc;
+    if (m >= 0) return base[(size_t)m * Nc + ni];
+    return conj(base[(size_t)(-m) * Nc + (Nc - 1 - ni)]);
+  }
+};
+template <class T>
+struct StRingMHalf {
+  cx<T>* R; int N, Nh; FastDiv fNh;
+  __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
+    const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh;
+    R[((size_t)b * N + k) * Nh + h] = v;
+  }
+};
+// Analysis, step over n (sign +1) with real output: rows a1 = 2 ap and a2 = 2 ap + 1 of
+// R[b][a][h], each extended Hermitian in n (n < 0: conjugate of -n), packed as x + i y;
+// the transform's real and imaginary parts are the two rows of W.
+template <class T>
+struct LdRingNHerm {
+  const cx<T>* R; int N, Nh, nstep, npair; FastDiv fP;
+  __device__ cx<T> operator()(int c, int j) const {
+    const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair), a2 = a1 + 1;
+    const int n = (j <= (N - 1) / 2) ? j : j - N;
+    const int an = n < 0 ? -n : n;
+    if (an & (nstep - 1)) return mk<T>(0, 0);
+    const int h = an >> (nstep - 1);
+    const cx<T>* rb = R + (size_t)b * N * Nh;
+    cx<T> x = rb[(size_t)a1 * Nh + h];
+    cx<T> y = (a2 < N) ? rb[(size_t)a2 * Nh + h] : mk<T>(0, 0);
+    if (n < 0) { x = conj(x); y = conj(y); }
+    return mk<T>(x.re - y.im, x.im + y.re);
   }
 };
 template <class T, class OutT>
-struct StWPair {
+struct StWRowPair {  // W[b][a][g], real: row a1 <- Re, a2 <- Im
   OutT* W; int N, npair; FastDiv fP;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
-    const int b = (int)fP.div(c), gp = c - b * npair, g1 = 2 * gp, g2 = g1 + 1;
-    const size_t idx = ((size_t)b * N + k) * N;
-    W[idx + g1] = (OutT)v.re;
-    if (g2 < N) W[idx + g2] = (OutT)v.im;
+    const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair), a2 = a1 + 1;
+    W[((size_t)b * N + a1) * N + k] = (OutT)v.re;
+    if (a2 < N) W[((size_t)b * N + a2) * N + k] = (OutT)v.im;
   }
 };
+// Synthesis, step over g (sign -1) of real rows in pairs (LdWRowPair), keeping n >= 0:
+// U[b][a][h] = D_n / N.
+template <class T>
+struct StRingNPairHalf {
+  cx<T>* U; int Nh, nstep, N, nrows; T scale;
+  __device__ void operator()(int c, int k, cx<T> z, cx<T> zn) const {
+    if (k > (N - 1) / 2 || (k & (nstep - 1))) return;  // n = k >= 0 in the n-set
+    const int h = k >> (nstep - 1);
+    if (h >= Nh) return;
+    const T hs = scale * (T)0.5;
+    U[(size_t)(2 * c) * Nh + h] = mk<T>((z.re + zn.re) * hs, (z.im - zn.im) * hs);
+    if (2 * c + 1 < nrows) U[(size_t)(2 * c + 1) * Nh + h] = mk<T>((z.im + zn.im) * hs, (zn.re - z.re) * hs);
+  }
+};
+template <class T> struct Mirror<StRingNPairHalf<T>> { static constexpr int value = 1; };
+// Synthesis, step over a (sign -1) for n >= 0: column (b, h) of U[b][a][h] -> D_m; the
+// m >= 0 outputs go to column ni of Xb, and conj(D_{-m}) to the mirror column (-n).
+template <class T>
+struct LdRingAHalf {
+  const cx<T>* U; int N, Nh; FastDiv fNh;
+  __device__ cx<T> operator()(int c, int j) const {
+    const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh;
+    return U[((size_t)b * N + j) * Nh + h];
+  }
+};
+template <class T>
+struct StRingAHalf {
+  cx<T>* Xb; int Mc, Nc, ni0, N, Nh; T scale; FastDiv fNh;
+  __device__ void operator()(int c, int k, cx<T> v, cx<T> vn) const {
+    if (k >= Mc) return;  // m = k >= 0 (Mc = Lb <= (N + 1) / 2)
+    const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh, ni = ni0 + h;
+    cx<T>* row = Xb + ((size_t)b * Mc + k) * Nc;
+    row[ni] = v * scale;
+    if (h > 0) row[Nc - 1 - ni] = conj(vn) * scale;
+  }
+};
+template <class T> struct Mirror<StRingAHalf<T>> { static constexpr int value = 1; };
 
 // SHT: map ring t -> F[t][mi] (1/N scaled), real or complex double map.
 struct LdMapRow {
