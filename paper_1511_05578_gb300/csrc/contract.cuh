@@ -225,8 +225,12 @@ static __global__ void sht_fwd_contract_kernel(const double* __restrict__ Q, int
   flm[l * l + l + m] = acc * nrm;
 }
 
+// Dynamic shared memory: Ls doubles (the normalisations sqrt((2l+1)/4pi)).
 static __global__ void sht_inv_contract_kernel(const double* __restrict__ Q, int Lmax, const cx<double>* __restrict__ flm,
                                         int Ls, int s, int Mc, int m0, cx<double>* __restrict__ G) {
+  extern __shared__ double nrm[];
+  for (int l = threadIdx.x; l < Ls; l += blockDim.x) nrm[l] = sqrt((2.0 * l + 1.0) / (4.0 * M_PI));
+  __syncthreads();
   const int mi = blockIdx.x * blockDim.x + threadIdx.x;
   const int mp = blockIdx.y;
   if (mi >= Mc) return;
@@ -234,7 +238,7 @@ static __global__ void sht_inv_contract_kernel(const double* __restrict__ Q, int
   cx<double> acc = mk(0.0, 0.0);
   int lstart = max(mp, max(abs(m), abs(s)));
   for (int l = lstart; l < Ls; ++l) {
-    const double d = sqrt((2.0 * l + 1.0) / (4.0 * M_PI)) * delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, -s);
+    const double d = nrm[l] * delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, -s);
     const cx<double> f = flm[l * l + l + m];
     acc.re += d * f.re; acc.im += d * f.im;
   }

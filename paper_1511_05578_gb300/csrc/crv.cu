@@ -496,7 +496,7 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   const int Mc = real ? Ls : N, m0 = real ? 0 : -(Ls - 1);
   dim3 g((Mc + 127) / 128, Ls);
   KTimer kt(K_SHT_CONTRACT, st);
-  sht_inv_contract_kernel<<<g, 128, 0, st>>>(p->dQ, p->L, flm, Ls, s, Mc, m0, p->wG);
+  sht_inv_contract_kernel<<<g, 128, (size_t)Ls * sizeof(double), st>>>(p->dQ, p->L, flm, Ls, s, Mc, m0, p->wG);
   kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};

@@ -8,6 +8,9 @@
 //   m' = 0..Lb-1              (X_{m n, -m'} = (-1)^{m+n} X_{m n m'}, so only m' >= 0 is kept)
 // Volumes are stored [row][mi][ni] with ni fastest.
 #pragma once
+#include <type_traits>
+#include <utility>
+
 #include "fft.cuh"
 
 namespace crv {
@@ -25,6 +28,15 @@ struct ColSet {
     return (m + n + extra) & 1;
   }
 };
+
+// L1 prefetch of a global address (no register results): loaders that define
+// pf(c, j) have the inputs of their next sequence fetched while the current one runs
+// (measured: faster for the ring rows, neutral for ring columns, and much slower for the
+// beta columns read from HBM at a stride of a whole (m, n) plane, which do without).
+__device__ __forceinline__ void pf_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+template <class Ld, class = void> struct HasPf { static constexpr bool value = false; };
+template <class Ld>
+struct HasPf<Ld, decltype(std::declval<const Ld&>().pf(0, 0), void())> { static constexpr bool value = true; };
 
 // ---------------------------------------------------------------------------
 // Batched DFTs of length N (Bluestein on the register FFT of fft.cuh). A block of
@@ -82,6 +94,16 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
       const int j = t + q * TP;
       v[q] = mk<T>(0, 0);
       if (q < 8 && valid && j < N) v[q] = ld(c, j) * chirp_of(tb, j, sign);
+    }
+    if constexpr (HasPf<Ld>::value) {
+      const int cn = c + s_step;
+      if (cn < s_end) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = t + q * TP;
+          if (j < N) ld.pf(cn, j);
+        }
+      }
     }
     fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
@@ -269,6 +291,10 @@ struct LdWRowPair {
     const T y = (r1 < nrows) ? (T)W[(size_t)r1 * N + j] : (T)0;
     return mk<T>(x, y);
   }
+  __device__ void pf(int c, int j) const {
+    pf_l1(W + (size_t)(2 * c) * N + j);
+    if (2 * c + 1 < nrows) pf_l1(W + (size_t)(2 * c + 1) * N + j);
+  }
 };
 template <class T>
 struct StRingNPair {
@@ -298,13 +324,18 @@ template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 
 template <class T>
 struct LdRingMHalf {
   const cx<T>* Xb; int Mc, Nc, ni0, N, Nh; FastDiv fNh;
-  __device__ cx<T> operator()(int c, int j) const {
+  __device__ const cx<T>* at(int c, int j, int& m) const {
     const int b = (int)fNh.div((uint32_t)c), ni = ni0 + (c - b * Nh);
-    const int m = (j <= (N - 1) / 2) ? j : j - N;
+    m = (j <= (N - 1) / 2) ? j : j - N;
     const cx<T>* base = Xb + (size_t)b * Mc * Nc;
-    if (m >= 0) return base[(size_t)m * Nc + ni];
-    return conj(base[(size_t)(-m) * Nc + (Nc - 1 - ni)]);
+    return m >= 0 ? base + (size_t)m * Nc + ni : base + (size_t)(-m) * Nc + (Nc - 1 - ni);
   }
+  __device__ cx<T> operator()(int c, int j) const {
+    int m;
+    const cx<T> v = *at(c, j, m);
+    return m >= 0 ? v : conj(v);
+  }
+  __device__ void pf(int c, int j) const { int m; pf_l1(at(c, j, m)); }
 };
 template <class T>
 struct StRingMHalf {
@@ -331,6 +362,15 @@ struct LdRingNHerm {
     cx<T> y = (a2 < N) ? rb[(size_t)a2 * Nh + h] : mk<T>(0, 0);
     if (n < 0) { x = conj(x); y = conj(y); }
     return mk<T>(x.re - y.im, x.im + y.re);
+  }
+  __device__ void pf(int c, int j) const {
+    const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair);
+    const int n = (j <= (N - 1) / 2) ? j : j - N;
+    const int an = n < 0 ? -n : n;
+    if (an & (nstep - 1)) return;
+    const cx<T>* q = R + (size_t)b * N * Nh + (size_t)a1 * Nh + (an >> (nstep - 1));
+    pf_l1(q);
+    if (a1 + 1 < N) pf_l1(q + Nh);
   }
 };
 template <class T, class OutT>
@@ -362,10 +402,12 @@ template <class T> struct Mirror<StRingNPairHalf<T>> { static constexpr int valu
 template <class T>
 struct LdRingAHalf {
   const cx<T>* U; int N, Nh; FastDiv fNh;
-  __device__ cx<T> operator()(int c, int j) const {
+  __device__ const cx<T>* at(int c, int j) const {
     const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh;
-    return U[((size_t)b * N + j) * Nh + h];
+    return U + ((size_t)b * N + j) * Nh + h;
   }
+  __device__ cx<T> operator()(int c, int j) const { return *at(c, j); }
+  __device__ void pf(int c, int j) const { pf_l1(at(c, j)); }
 };
 template <class T>
 struct StRingAHalf {
