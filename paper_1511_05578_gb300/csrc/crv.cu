@@ -394,12 +394,12 @@ static int num_sms() {
 
 // Persistent FFT blocks (one or two per SM, by shared memory and registers), each
 // looping over groups of G sequences.
-template <class T, int NT, bool COLS, int PT, bool SPAN, class Ld, class St>
+template <class T, int NT, bool COLS, int PT, class Ld, class St>
 static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld, St st, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
-  auto kern = dft_kernel<T, NT, COLS, PT, SPAN, Ld, St>;
+  auto kern = dft_kernel<T, NT, COLS, PT, Ld, St>;
   if (!set_smem(kern, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
   const int grid = std::max(1, std::min((nseq + G - 1) / G, num_sms() * bps));
@@ -408,20 +408,14 @@ static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld,
   kt.done();
   return launch_ok(kind_name(kind));
 }
-// WIDE: columns of a large volume (the beta transforms over all (m, n)), read from HBM:
-// two adjacent columns per block and a contiguous run of columns per block (reuse of
-// each sector through L1). Ring columns (read from the L2-resident ring buffer, written
-// into the large W or Xb volumes) and rows run faster with two 256-thread blocks per SM
-// striding together, so that each output sector is filled at about one time (measured).
-template <class T, bool COLS, bool WIDE = false, class Ld, class St>
+// FP32: 256 threads (two blocks per SM); FP64: 256 threads, one block per SM. The lengths
+// of the two largest band limits get kernels compiled for their P.
+template <class T, bool COLS, class Ld, class St>
 static bool run_dft(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld, St st, cudaStream_t s) {
   if (nseq <= 0) return true;
-  // FP32: 256 threads (two blocks per SM), 512 for WIDE columns. FP64: 256 threads, one
-  // block per SM. The lengths of the two largest band limits get kernels compiled for their P.
-  constexpr int NT = (sizeof(T) == 4 && COLS && WIDE) ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_dft_nt<T, NT, COLS, 4096, WIDE>(kind, tb, sign, nseq, ld, st, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_dft_nt<T, NT, COLS, 2048, WIDE>(kind, tb, sign, nseq, ld, st, s);
-  return run_dft_nt<T, NT, COLS, 0, WIDE>(kind, tb, sign, nseq, ld, st, s);
+  if (sizeof(T) == 4 && tb.P == 4096) return run_dft_nt<T, 256, COLS, 4096>(kind, tb, sign, nseq, ld, st, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_dft_nt<T, 256, COLS, 2048>(kind, tb, sign, nseq, ld, st, s);
+  return run_dft_nt<T, 256, COLS, 0>(kind, tb, sign, nseq, ld, st, s);
 }
 template <class T, class Ld, class St>
 static bool run_rows(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
@@ -431,9 +425,33 @@ template <class T, class Ld, class St>
 static bool run_cols(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
   return run_dft<T, true>(kind, tb, sign, n, ld, st, s);
 }
-template <class T, class Ld, class St>
-static bool run_cols_wide(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St st, cudaStream_t s) {
-  return run_dft<T, true, true>(kind, tb, sign, n, ld, st, s);
+
+// Beta transforms: 512 FP32 threads (two adjacent column pairs per load), each block on a
+// contiguous run of pairs (neighbouring columns share sectors through L1; measured).
+template <class T, int NT, int PT>
+static bool run_beta_synth_nt(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* X, cx<T>* Y, ColSet cs,
+                              int kind, cudaStream_t s) {
+  const int G = NT / (tb.P / 16);
+  if (G < 1) { g_err = "FFT length too large for the block"; return false; }
+  const size_t smem = fft_smem_bytes<T>(NT);
+  if (!set_smem(beta_synth_kernel<T, NT, PT>, smem)) return false;
+  const int bps = FftMinBlocks<T, NT>::value;
+  const int npair = num_col_pairs(cs);
+  const int grid = std::max(1, std::min((npair + G - 1) / G, num_sms() * bps));
+  KTimer kt(kind, s);
+  beta_synth_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ncols, Lb, X, Y, cs);
+  kt.done();
+  return launch_ok("beta_synth_kernel");
+}
+// Synthesis over beta of all column pairs: X[m'][c] -> Y[b][c].
+template <class T>
+static bool run_beta_synth(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* X, cx<T>* Y, ColSet cs, int kind,
+                           cudaStream_t s) {
+  if (ncols <= 0) return true;
+  constexpr int NT = sizeof(T) == 4 ? 512 : 256;
+  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_synth_nt<T, NT, 4096>(tb, Lb, ncols, X, Y, cs, kind, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_synth_nt<T, NT, 2048>(tb, Lb, ncols, X, Y, cs, kind, s);
+  return run_beta_synth_nt<T, NT, 0>(tb, Lb, ncols, X, Y, cs, kind, s);
 }
 
 template <class T, int NT, int PT>
@@ -500,9 +518,7 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
-  LdBetaSynthPair<double> lb{p->wG, Mc, Ls, N, cs, fs.d.hphase};
-  StRowsPair<double> sr{p->wF, Mc, Ls, cs};
-  if (!run_cols<double>(K_BETA_SYNTH, fs.d, +1, num_col_pairs(cs), lb, sr, st)) return false;
+  if (!run_beta_synth<double>(fs.d, Ls, Mc, p->wG, p->wF, cs, K_BETA_SYNTH, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
   StMapRow sm{map, N, real};
   return run_rows<double>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
@@ -548,10 +564,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = cs.Mc * cs.Nc;
-  if (!run_cols_wide<T>(K_BETA_SYNTH, dft_of<T>(fs), +1, num_col_pairs(cs),
-                        LdBetaSynthPair<T>{X, ncols, Lb, N, cs, dft_of<T>(fs).hphase}, StRowsPair<T>{Xb, ncols, Lb, cs},
-                        st))
-    return false;
+  if (!run_beta_synth<T>(dft_of<T>(fs), Lb, ncols, X, Xb, cs, K_BETA_SYNTH, st)) return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
   const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0

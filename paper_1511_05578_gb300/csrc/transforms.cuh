@@ -48,8 +48,8 @@ struct HasPf<Ld, decltype(std::declval<const Ld&>().pf(0, 0), void())> { static 
 //   transforms of a block interleave their threads (g fastest), so each load or
 //   store touches G adjacent sequences, and the exchange buffers interleave too.
 // Storers get st(c, k, X_k, X_k') for every k < N, where k' is set by Mirror<St>:
-// 0: no partner (X_k' = X_k), 1: k' = (N - k) mod N (real-pair unpacking), 2: k' = N - 1 - k
-// (beta-reflection pairs); the partner is gathered through shared memory.
+// 0: no partner (X_k' = X_k), 1: k' = (N - k) mod N (real-pair unpacking), 2: k' = N - 1 - k;
+// the partner is gathered through shared memory.
 // ---------------------------------------------------------------------------
 template <class St> struct Mirror { static constexpr int value = 0; };
 
@@ -69,11 +69,10 @@ __device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned
 // Blocks of NT threads; FP32 blocks of 256 threads fit twice on an SM (<= 128 registers).
 template <class T, int NT> struct FftMinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1; };
 
-// PT: P as a compile-time constant, or 0 (from the table). SPAN: each block takes one
-// contiguous run of sequences (neighbouring columns then share sectors through L1), else
-// blocks stride through the sequences together (neighbouring blocks fill each sector of
-// a large output at about the same time).
-template <class T, int NT, bool COLS, int PT, bool SPAN, class Ld, class St>
+// PT: P as a compile-time constant, or 0 (from the table). Blocks stride through the
+// sequences together, so that neighbouring blocks fill each sector of a large output at
+// about the same time (measured faster than contiguous runs per block here).
+template <class T, int NT, bool COLS, int PT, class Ld, class St>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(DftTab<T> tb, int sign, int nseq, Ld ld, St st) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
@@ -81,11 +80,8 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
   XBuf2<T> buf;
   fft_slot<T, NT, COLS, PT>(g, t, buf, smraw, tb.P);
   const cx<T>* __restrict__ kh = (sign < 0) ? tb.khat_f : tb.khat_i;
-  const int span = SPAN ? (nseq + gridDim.x * G - 1) / (gridDim.x * G) * G : G;
-  const int s_beg = SPAN ? blockIdx.x * span : blockIdx.x * G;
-  const int s_end = SPAN ? min(nseq, (blockIdx.x + 1) * span) : nseq;
-  const int s_step = SPAN ? G : gridDim.x * G;
-  for (int s0 = s_beg; s0 < s_end; s0 += s_step) {
+  const int s_end = nseq, s_step = gridDim.x * G;
+  for (int s0 = blockIdx.x * G; s0 < s_end; s0 += s_step) {
     const int c = s0 + g;
     const bool valid = c < nseq;
     cx<T> v[16];
@@ -159,36 +155,6 @@ __device__ __forceinline__ ColPair col_pair(const ColSet& cs, int p) {
 }
 __host__ __device__ inline int num_col_pairs(const ColSet& cs) { return (cs.Mc + 1) / 2 * cs.Nc; }
 
-// Synthesis over beta of a column pair: z_j = (X~A + X~B)_{m'} e^{i m' pi/N}.
-template <class T>
-struct LdBetaSynthPair {
-  const cx<T>* X; int C, K, N; ColSet cs; const cx<T>* hphase;
-  __device__ cx<T> operator()(int p, int j) const {
-    const ColPair cp = col_pair(cs, p);
-    const int mp = (j < K) ? j : j - N;
-    const int a = mp < 0 ? -mp : mp;
-    cx<T> v = X[(size_t)a * C + cp.cA];
-    if (mp < 0 && cp.parA) v = mk(-v.re, -v.im);
-    if (cp.cB >= 0) {
-      const cx<T> w = X[(size_t)a * C + cp.cB];
-      v = (mp < 0 && !cp.parA) ? v - w : v + w;
-    }
-    return v * hphase[j];
-  }
-};
-// F_A, F_B = (F_b +- F_{N-1-b}) / 2 (the symmetric half to the even-parity column), b < Kout.
-template <class T>
-struct StRowsPair {
-  cx<T>* Y; int C, Kout; ColSet cs;
-  __device__ void operator()(int p, int k, cx<T> v, cx<T> vr) const {
-    if (k >= Kout) return;
-    const ColPair cp = col_pair(cs, p);
-    const cx<T> sym = (v + vr) * (T)0.5, anti = (v - vr) * (T)0.5;
-    Y[(size_t)k * C + cp.cA] = cp.parA ? anti : sym;
-    if (cp.cB >= 0) Y[(size_t)k * C + cp.cB] = cp.parA ? sym : anti;
-  }
-};
-template <class T> struct Mirror<StRowsPair<T>> { static constexpr int value = 2; };
 
 // Ring inverse, step over n: row (b, mi) of Xb (Nc contiguous) -> T[b][mi][g].
 template <class T>
@@ -467,6 +433,105 @@ struct StMapRow {
 };
 
 // ---------------------------------------------------------------------------
+// Extension of a column pair to the 2Lb-1 nodes of the full circle (beta transforms).
+// Rows i < Lb of the two columns are loaded once (they sit in v[0..3]: Lb <= P/4), and
+// the reflected half, sA (A - B) with sA = (-1)^{parA}, comes back through shared memory:
+//   v[q] = (A + B)_j for j < Lb,  sA (A - B)_{N - off - j} for Lb <= j < N, 0 beyond,
+// with off = 0 when index 0 is its own mirror (m' -> -m') and off = 1 for the reflection
+// b -> N - 1 - b of the ring samples.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void load_pair_ext(cx<T> (&v)[16], const cx<T>* __restrict__ X, int C, const ColPair& cp,
+                                              bool valid, int Lb, int N, int t, int TP, int off, XBuf2<T>& buf) {
+  cx<T> d[4];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = mk<T>(0, 0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = t + q * TP;
+    d[q] = mk<T>(0, 0);
+    if (valid && j < Lb) {
+      const cx<T>* row = X + (size_t)j * C;
+      const cx<T> a = row[cp.cA];
+      const cx<T> b = cp.cB >= 0 ? row[cp.cB] : mk<T>(0, 0);
+      v[q] = a + b;
+      d[q] = cp.parA ? b - a : a - b;
+    }
+  }
+  const XBuf<T> x = buf.take();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = t + q * TP;
+    if (j < Lb) x[j] = d[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int j = t + q * TP;
+    if (j >= Lb && j < N) v[q] = x[N - off - j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Synthesis over beta of a column pair (Eq. inverse_feul, the m' -> beta step):
+// z_{m'} = (X~A + X~B)_{m'} e^{i m' pi/N} on m' in (-Lb, Lb), X~_{-m'} = (-1)^{m+n+extra} X~_{m'};
+// F_b = sum_{m'} z_{m'} e^{2 pi i m' b/N}; the symmetric half (F_b + F_{N-1-b})/2 belongs to the
+// column of even parity, the antisymmetric half to the other. In: X[m'][c] (m' < Lb);
+// out: Y[b][c] (b < Lb). Threads as in dft_kernel with COLS.
+// ---------------------------------------------------------------------------
+template <class T, int NT, int PT>
+__global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_kernel(DftTab<T> tb, int ncols, int Lb,
+                                                                     const cx<T>* __restrict__ X,
+                                                                     cx<T>* __restrict__ Y, ColSet cs) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = tb.N, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
+  const int npair = num_col_pairs(cs);
+  int g, t;
+  XBuf2<T> buf;
+  fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
+  const int span = (npair + gridDim.x * G - 1) / (gridDim.x * G) * G;
+  const int s_end = min(npair, (blockIdx.x + 1) * span);
+  for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
+    const int p = s0 + g;
+    const bool valid = p < s_end;
+    const ColPair cp = valid ? col_pair(cs, p) : ColPair{0, -1, 0};
+    cx<T> v[16];
+    load_pair_ext<T>(v, X, ncols, cp, valid, Lb, N, t, TP, 0, buf);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = t + q * TP;
+      if (j < N) v[q] = v[q] * tb.hphase[j] * chirp_of(tb, j, +1);
+    }
+    fft16<-1, true, PT>(v, tb, buf, t);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * tb.khat_i[t + q * TP];
+    fft16<+1, false, PT>(v, tb, buf, t);
+    const XBuf<T> y = buf.take();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int k = t + q * TP;
+      if (k < N) {
+        v[q] = v[q] * chirp_of(tb, k, +1);
+        y[k] = v[q];
+      }
+    }
+    __syncthreads();
+    if (valid) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = t + q * TP;
+        if (k < Lb) {
+          const cx<T> r = y[N - 1 - k];
+          const cx<T> sym = (v[q] + r) * (T)0.5, anti = (v[q] - r) * (T)0.5;
+          Y[(size_t)k * ncols + cp.cA] = cp.parA ? anti : sym;
+          if (cp.cB >= 0) Y[(size_t)k * ncols + cp.cB] = cp.parA ? sym : anti;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Exact quadrature over beta (Eqs. TildaFmn, Fmnmp, gmnmp), folded onto m' >= 0, for a
 // column pair (ColPair): extend the Lb ring values of each column to 2Lb-1 with
 // (-1)^{m+n+extra} and add the two, DFT (sign -1, half-sample phase e^{-i m'' pi/N}/N),
@@ -500,20 +565,11 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     const ColPair cp = valid ? col_pair(cs, p) : ColPair{0, -1, 0};
     // extensions to the 2Lb-1 nodes of the full circle, summed, then the chirp
     cx<T> v[16];
+    load_pair_ext<T>(v, Xb, ncols, cp, valid, Lb, N, t, TP, 1, buf);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int j = t + q * TP;
-      v[q] = mk<T>(0, 0);
-      if (q < 8 && valid && j < N) {
-        const size_t row = (size_t)(j < Lb ? j : N - 1 - j) * ncols;
-        cx<T> x = Xb[row + cp.cA];
-        if (j >= Lb && cp.parA) x = mk(-x.re, -x.im);
-        if (cp.cB >= 0) {
-          const cx<T> y = Xb[row + cp.cB];
-          x = (j >= Lb && !cp.parA) ? x - y : x + y;
-        }
-        v[q] = x * chirp_of(tb, j, -1);
-      }
+      if (j < N) v[q] = v[q] * chirp_of(tb, j, -1);
     }
     fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
