@@ -25,10 +25,14 @@ static_assert(BNC == TC_TILE_ROWS, "table tiles are accumulator tiles");
 // ---------------------------------------------------------------------------
 // Problems: operand builders, K ranges and epilogues
 // ---------------------------------------------------------------------------
+// Quad q of the K step starting at k0 (a multiple of BK) of row c, from a table chunk of
+// TC_CHUNK_K columns.
 __device__ __forceinline__ void tab4(const TcTab& tb, int mp, int tile, int k0, int c, int q, float* x) {
-  const long long chunk = tb.base[mp * tb.ntiles + tile] + (k0 >> 5);
+  static_assert(TC_CHUNK_K % BK == 0, "engine steps tile the table chunks");
+  const long long chunk = tb.base[mp * tb.ntiles + tile] + k0 / TC_CHUNK_K;
+  const int qq = q + (k0 % TC_CHUNK_K) / 4;
   const float4 v = __ldg(reinterpret_cast<const float4*>(tb.data + (size_t)chunk * TC_CHUNK_FLOATS + (c >> 3) * 256 +
-                                                         q * 32 + (c & 7) * 4));
+                                                         qq * 32 + (c & 7) * 4));
   x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
 }
 

@@ -3,11 +3,13 @@
 // D[128 x BN] = sum_k A[128 x k] B[BN x k]^T with FP32 operands produced on the fly by a
 // problem object. Each operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a
 // K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM accumulator (split-FP32,
-// ~2^-22 per product). All 512 threads build the operand stage in shared memory in the
+// ~2^-22 per product). All 256 threads build the operand stage in shared memory in the
 // canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered,
 // with the next chunk's loads in flight; one thread issues tcgen05.mma and commits to the
 // stage's mbarrier; waits are bounded and set an error flag instead of hanging; all
-// warps drain TMEM with tcgen05.ld.
+// warps drain TMEM with tcgen05.ld. Stages of K = 16 keep a CTA at ~98 KB of shared
+// memory and 256 TMEM columns, so two CTAs share an SM and one's prologue and epilogue
+// overlap the other's MMAs.
 #pragma once
 #include <cstdint>
 
@@ -16,8 +18,9 @@
 namespace crv {
 namespace tc {
 
-constexpr int BM = 128, BK = 32, STAGES = 2, NT = 512;
-constexpr int A_BYTES = BM * BK * 4;             // 16 KB per A tile (hi or lo)
+constexpr int BM = 128, BK = 16, STAGES = 2, NT = 256;
+constexpr int A_BYTES = BM * BK * 4;             // 8 KB per A tile (hi or lo)
+constexpr int GROUP_BYTES = BK / 4 * 128;       // one 8-row group of core matrices (512 B)
 constexpr long kWaitLimit = 1L << 22;            // bounded spin on mbarriers
 
 // Tile geometry for an accumulator of BN columns (BN in {64, 128, 192, 256}).
@@ -34,15 +37,17 @@ struct Geo {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of the 16-byte chunk (row r, k-quad q) in a [rows x 32] tf32 tile:
+// byte offset of the 16-byte chunk (row r, k-quad q) in a [rows x BK] tf32 tile:
 // core matrix (8 rows x 16 B) at (r/8, q); K-adjacent core matrices 128 B apart,
-// 8-row groups 1024 B apart.
-__device__ __forceinline__ uint32_t chunk_off(int r, int q) { return (uint32_t)((r >> 3) * 1024 + q * 128 + (r & 7) * 16); }
+// 8-row groups GROUP_BYTES apart.
+__device__ __forceinline__ uint32_t chunk_off(int r, int q) {
+  return (uint32_t)((r >> 3) * GROUP_BYTES + q * 128 + (r & 7) * 16);
+}
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
   d |= (uint64_t)(128u >> 4) << 16;   // leading byte offset: next core matrix along K
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)((uint32_t)GROUP_BYTES >> 4) << 32;  // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;             // descriptor version for tcgen05
   return d;                           // base offset 0, no swizzle
 }
@@ -126,7 +131,7 @@ __device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a
 //   Prob::zero16(z, r0, c0, r, cc)            same for a tile with an empty K range
 // ---------------------------------------------------------------------------
 template <class Prob, int BN>
-__global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(Prob pb, int* err) {
+__global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   using G = Geo<BN>;
   constexpr int B_BYTES = G::B_BYTES, STAGE_BYTES = G::STAGE_BYTES;
   extern __shared__ unsigned char smraw[];
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(NT, 1) tc_gemm_kernel(Prob pb, int* err) {
   const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  // Operand quads of one K chunk per thread: A 128 rows x 8 k-quads, B BN rows x 8 k-quads.
+  // Operand quads of one K chunk per thread: A 128 rows x BK/4 k-quads, B BN rows x BK/4.
   // The loads of chunk c + 1 are issued as soon as chunk c is in shared memory, so their
   // latency overlaps the barrier and the MMAs of chunk c.
   constexpr int NA = BM * (BK / 4) / NT, NB = BN * (BK / 4) / NT;
