@@ -629,7 +629,7 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   if constexpr (sizeof(T) == 4) {
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
     if (p->use_tc)
-      return tc_synthesis(p->dQ, p->L, (const cx<float>*)Y, p->tabS[j], Lb, cs, (cx<float>*)p->wXb, flm, p->d_err,
+      return tc_synthesis(p->dQ32, p->L, (const cx<float>*)Y, p->tabS[j], Lb, cs, (cx<float>*)p->wXb, flm, p->d_err,
                           st);
   }
   const int mchunk = 16;

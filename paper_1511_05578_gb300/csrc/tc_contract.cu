@@ -137,60 +137,39 @@ struct SynthesisProb {
   __device__ void zero16(int, int, int, int, int) const {}  // tiles without work are never read
 };
 
-// f_lm += sum_{m' <= l} Delta^l_{m'm} Z[m'][mi][l] in FP64 (FP64 Delta table).
-// Block = 32 (mi) x 32 (l) outputs, 256 threads, m' loop with shared-memory tiles.
-__global__ void __launch_bounds__(256) synth_reduce_kernel(const double* __restrict__ Q, int Lmax,
+// f_lm += sum_{m' <= l} Delta^l_{m'm} Z[m'][mi][l] (Eq. flml's sum over m'), one thread per
+// (l, m), threads of a block along l (Z reads coalesced). Delta^l_{m'm} is read as
+// Delta^l_{|m| m'} from the FP32 table, contiguous in m' for each thread: with
+// Delta^l_{m'm} = (-1)^{m'-m} Delta^l_{mm'} and Delta^l_{m',-n} = (-1)^{l+m'} Delta^l_{m'n},
+//   m >= 0: Delta^l_{m'm} = (-1)^{m'+m} Q[m][l][m'],   m < 0: (-1)^{l+|m|} Q[|m|][l][m'].
+// Products and partial sums in FP32, flushed into an FP64 accumulator every 32 terms;
+// f_lm accumulates in FP64.
+__global__ void __launch_bounds__(256) synth_reduce_kernel(const float* __restrict__ Q32, int Lmax,
                                                           const cx<float>* __restrict__ Z, int Lb, ColSet cs,
                                                           cx<double>* __restrict__ flm) {
-  __shared__ cx<float> Zs[32][33];
-  __shared__ double Qs[32][33];  // [l][|m|]
-  const int l0 = blockIdx.x * 32, mi0 = blockIdx.y * 32;
-  const int lhi = min(l0 + 32, Lb) - 1;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // ty: 8 rows of mi per pass
-  const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + 32, cs.Mc) - 1;
-  const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
-  if (amin > lhi) return;
-  cx<double> acc[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) acc[i] = mk(0.0, 0.0);
-  for (int mp = 0; mp <= lhi; ++mp) {
-    // Z rows: [mi0 + i][l0 + tx]
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int mi = mi0 + ty + 8 * i, l = l0 + tx;
-      Zs[ty + 8 * i][tx] = (mi < cs.Mc && l < Lb) ? Z[((size_t)mp * cs.Mc + mi) * Lb + l] : mk<float>(0, 0);
+  const int l = blockIdx.x * blockDim.x + threadIdx.x, mi = blockIdx.y;
+  const int m = cs.m0 + mi, am = m < 0 ? -m : m;
+  if (l >= Lb || am > l) return;
+  const float* __restrict__ q = Q32 + ((size_t)am * Lmax + l) * Lmax;  // q[m'] = Delta^l_{|m| m'}
+  const cx<float>* __restrict__ z = Z + (size_t)mi * Lb + l;           // z[m' * Mc * Lb]
+  const size_t zs = (size_t)cs.Mc * Lb;
+  cx<double> acc = mk(0.0, 0.0);  // sum over even m' minus (m >= 0) / plus (m < 0) odd m'
+  const float so = m >= 0 ? -1.f : 1.f;
+  for (int m0 = 0; m0 <= l; m0 += 32) {
+    float er = 0.f, ei = 0.f;
+    const int mend = min(m0 + 32, l + 1);
+    for (int mp = m0; mp < mend; ++mp) {
+      const float d = (mp & 1) ? so * __ldg(q + mp) : __ldg(q + mp);
+      const cx<float> v = z[(size_t)mp * zs];
+      er = fmaf(d, v.re, er);
+      ei = fmaf(d, v.im, ei);
     }
-    // Delta rows: [l0 + i][|m| for the 32 m of the tile]; m = m0 + mi0 + tx
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int l = l0 + ty + 8 * i, m = cs.m0 + mi0 + tx;
-      double v = 0.0;
-      if (l < Lb && l >= mp && mi0 + tx < cs.Mc && abs(m) <= l) {
-        v = Q[((size_t)mp * Lmax + l) * Lmax + abs(m)];
-        if (m < 0 && ((l + mp) & 1)) v = -v;
-      }
-      Qs[ty + 8 * i][tx] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int mloc = ty + 8 * i;  // thread owns (mi0 + mloc, l0 + tx)
-      const double d = Qs[tx][mloc];
-      const cx<float> z = Zs[mloc][tx];
-      acc[i].re += d * (double)z.re;
-      acc[i].im += d * (double)z.im;
-    }
-    __syncthreads();
+    acc.re += (double)er;
+    acc.im += (double)ei;
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int mi = mi0 + ty + 8 * i, l = l0 + tx;
-    if (mi >= cs.Mc || l >= Lb) continue;
-    const int m = cs.m0 + mi;
-    if (abs(m) > l) continue;
-    cx<double>& f = flm[l * l + l + m];
-    f = f + acc[i];
-  }
+  const bool neg = m >= 0 ? (am & 1) : ((l + am) & 1);
+  cx<double>& f = flm[l * l + l + m];
+  f = neg ? f - acc : f + acc;
 }
 
 // Table fills: block (tile, m'), thread = row of the 256-row chunks.
@@ -302,14 +281,14 @@ bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int
   return launch_tc_gemm<tc::AnalysisProb, tc::BNC>(pb, grid, err, st, K_TC_A);
 }
 
-bool tc_synthesis(const double* Q64, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
+bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
                   cx<double>* flm, int* err, cudaStream_t st) {
   tc::SynthesisProb pb{Y, tb, Lb, cs, Zscratch};
   dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
   if (!launch_tc_gemm<tc::SynthesisProb, tc::BNC>(pb, grid, err, st, K_TC_S)) return false;
-  dim3 g2((Lb + 31) / 32, (cs.Mc + 31) / 32);
+  dim3 g2((Lb + 255) / 256, cs.Mc);
   KTimer kt(K_TC_S, st);
-  tc::synth_reduce_kernel<<<g2, 256, 0, st>>>(Q64, Lmax, Zscratch, Lb, cs, flm);
+  tc::synth_reduce_kernel<<<g2, 256, 0, st>>>(Q32, Lmax, Zscratch, Lb, cs, flm);
   kt.done();
   return launch_ok("synth_reduce_kernel");
 }

@@ -35,7 +35,7 @@ bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int L
 
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
                  int* err, cudaStream_t st);
-bool tc_synthesis(const double* Q64, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
+bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
                   cx<double>* flm, int* err, cudaStream_t st);
 
 }  // namespace crv
