@@ -534,10 +534,13 @@ template <class T> static const T* psi_of(crv_plan_s* p, int j);
 template <> const double* psi_of<double>(crv_plan_s* p, int j) { return p->dpsi[j]; }
 template <> const float* psi_of<float>(crv_plan_s* p, int j) { return p->dpsi32[j]; }
 
-// Rings per chunk of the ring buffer (rows padded to N + 1 elements in the analysis).
+// Rings per chunk of the ring buffer: real signals hold [a][h] (N x Nh) per ring, complex
+// ones [m][g] with rows padded to N + 1 (analysis) or [a][n] (synthesis).
 static int ring_chunk(crv_plan_s* p, int Lb, size_t elem) {
   const int N = 2 * Lb - 1;
-  const size_t per = (size_t)(N + 1) * std::max(p->mc(Lb), p->nc(Lb)) * elem;
+  const ColSet cs = p->colset(Lb);
+  const size_t per = p->real ? (size_t)N * (cs.Nc - (-cs.n0 / cs.nstep)) * elem
+                             : (size_t)(N + 1) * std::max(p->mc(Lb), p->nc(Lb)) * elem;
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lb, p->ring_bytes / per));
 }
 
