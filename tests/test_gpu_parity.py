@@ -116,6 +116,20 @@ def test_analysis_synthesis_tiny_and_degenerate():
     _analysis_parity(3, 2.0, 2, 0, False, 0, 1e-12)
 
 
+def test_analysis_synthesis_fp64_real_odd_L():
+    """Real spin-0 map with odd band limits (L=33): the last (m, m+1) column pair of the beta
+    transforms has no partner, and the n >= 0 half of the ring transforms is uneven."""
+    e = _analysis_parity(33, 2.0, 2, 0, True, crv.CRV_F_REAL, 1e-10, seed=3)
+    assert e["roundtrip"] < 1e-12
+
+
+def test_mixed_precision_real_odd_L_lambda():
+    """Mixed precision, real spin 0, L=45, lambda=1.7, J0=1: odd and non-power-of-two band
+    limits through the tensor-core tables and the paired beta kernels."""
+    e = _analysis_parity(45, 1.7, 1, 0, True, crv.CRV_F_REAL | crv.CRV_F_MIXED, 1e-5, seed=4)
+    assert e["roundtrip"] < 1e-5
+
+
 def test_mixed_precision_L64():
     e = _analysis_parity(64, 2.0, 2, 0, True, crv.CRV_F_REAL | crv.CRV_F_MIXED, 1e-5)
     assert e["roundtrip"] < 1e-5
