@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) contract_analysis_kernel(const T* __restr
     }
     __syncthreads();
   }
-  const size_t plane = (size_t)cs.Mc * cs.Nc;
+  const size_t plane = cs.pitch();
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     const int mi = mi0 + ty * 2 + i;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) contract_analysis_kernel(const T* __restr
       const int ni = ni0 + tx * 4 + j;
       if (ni >= cs.Nc) continue;
       const int n = cs.n0 + cs.nstep * ni;
-      X[(size_t)mp * plane + (size_t)mi * cs.Nc + ni] = mul_ipow(acc[i][j], imod(n - m, 4));
+      X[(size_t)mp * plane + cs.col(mi, ni)] = mul_ipow(acc[i][j], imod(n - m, 4));
     }
   }
 }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) contract_synthesis_kernel(const T* __rest
   cx<double> facc[2][2];
 #pragma unroll
   for (int i = 0; i < 2; ++i) { facc[i][0] = mk(0.0, 0.0); facc[i][1] = mk(0.0, 0.0); }
-  const size_t plane = (size_t)cs.Mc * cs.Nc;
+  const size_t plane = cs.pitch();
   const int mp_end = min((int)(blockIdx.z + 1) * mchunk, lhi + 1);
   for (int mp = blockIdx.z * mchunk; mp < mp_end; ++mp) {
     cx<T> z[2][2];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) contract_synthesis_kernel(const T* __rest
     for (int nk = ni_lo; nk < ni_hi; nk += TK) {
       for (int t = threadIdx.x; t < TM * TK; t += 256) {
         const int i = t / TK, k = t % TK, mi = mi0 + i, ni = nk + k;
-        Ys[i][k] = (mi < cs.Mc && ni < ni_hi) ? Y[(size_t)mp * plane + (size_t)mi * cs.Nc + ni] : mk<T>(0, 0);
+        Ys[i][k] = (mi < cs.Mc && ni < ni_hi) ? Y[(size_t)mp * plane + cs.col(mi, ni)] : mk<T>(0, 0);
       }
       for (int t = threadIdx.x; t < TK * TL; t += 256) {
         const int k = t / TL, j = t % TL, ni = nk + k, l = l0 + j;

@@ -566,7 +566,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     kt.done();
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
-  const int ncols = cs.Mc * cs.Nc;
+  const int ncols = (int)cs.pitch();
   if (!run_beta_synth<T>(dft_of<T>(fs), Lb, ncols, X, Xb, cs, K_BETA_SYNTH, st)) return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
@@ -575,7 +575,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     const int nr = std::min(Rr, Lb - b0);
     if (p->real) {
       // m step on the n >= 0 columns, then the n step with real output, rows in pairs
-      LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.Nc, ni0, N, Nh, FastDiv((uint32_t)Nh)};
+      LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, FastDiv((uint32_t)Nh)};
       StRingMHalf<T> sm{R, N, Nh, FastDiv((uint32_t)Nh)};
       if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nh, lm, sm, st)) return false;
       const int npair = (N + 1) / 2;
@@ -583,7 +583,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
       StWRowPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
       if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * npair, ln, sw, st)) return false;
     } else {
-      LdRingN<T> ln{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Nc, cs.n0, cs.nstep, N};
+      LdRingN<T> ln{Xb + (size_t)b0 * cs.pitch(), cs, N, FastDiv((uint32_t)cs.Mc)};
       StContig<T> sc{R, N + 1};
       if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
       LdRingM<T> lm{R, cs.Mc, cs.m0, N, N + 1, false, FastDiv((uint32_t)N)};
@@ -615,19 +615,18 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
       StRingNPairHalf<T> sn{R, Nh, cs.nstep, N, nrows, (T)1 / (T)N};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, (nrows + 1) / 2, lw, sn, st)) return false;
       LdRingAHalf<T> la{R, N, Nh, FastDiv((uint32_t)Nh)};
-      StRingAHalf<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.Nc, ni0, N, Nh, (T)1 / (T)N,
-                        FastDiv((uint32_t)Nh)};
+      StRingAHalf<T> sa{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, (T)1 / (T)N, FastDiv((uint32_t)Nh)};
       if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * Nh, la, sa, st)) return false;
     } else {
       LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, false};
       StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, nr * N, lw, sn, st)) return false;
       LdRingA<T> la{R, cs.Nc, N, FastDiv((uint32_t)cs.Nc)};
-      StRingA<T> sa{Xb + (size_t)b0 * cs.Mc * cs.Nc, cs.Mc, cs.m0, cs.Nc, N, (T)1 / (T)N, FastDiv((uint32_t)cs.Nc)};
+      StRingA<T> sa{Xb + (size_t)b0 * cs.pitch(), cs, N, (T)1 / (T)N};
       if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * cs.Nc, la, sa, st)) return false;
     }
   }
-  const int ncols = cs.Mc * cs.Nc;
+  const int ncols = (int)cs.pitch();
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
   if constexpr (sizeof(T) == 4) {
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
@@ -882,7 +881,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   // workspace
   const int Mc = p->mc(L), Nc = p->nc(L), N = 2 * L - 1;
   const size_t el = p->mixed ? sizeof(cx<float>) : sizeof(cx<double>);
-  p->vol_bytes = (size_t)L * Mc * Nc * el;
+  p->vol_bytes = (size_t)L * p->colset(L).pitch() * el;  // (m, n) planes with pair-interleaved columns
   p->wflm = p->dalloc<cx<double>>((size_t)L * L, &stt);
   p->wflm2 = p->dalloc<cx<double>>((size_t)L * L, &stt);
   p->wflm32 = p->dalloc<cx<float>>((size_t)L * L, &stt);

@@ -73,7 +73,7 @@ struct AnalysisProb {
     for (int i = 0; i < 16; ++i) other[i] = __shfl_xor_sync(0xffffffffu, d[i], 1);
     if (mi >= cs.Mc) return;
     const int m = cs.m0 + mi;
-    const size_t rowbase = ((size_t)mp * cs.Mc + mi) * cs.Nc;
+    cx<float>* plane = X + (size_t)mp * cs.pitch();
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int c = c0 + (odd ? 8 : 0) + i;
@@ -82,7 +82,7 @@ struct AnalysisProb {
       const float re = odd ? other[8 + i] : d[i];
       const float im = odd ? d[8 + i] : other[i];
       const int n = cs.n0 + cs.nstep * ni;
-      X[rowbase + ni] = mul_ipow(mk<float>(re, im), imod(n - m, 4));
+      plane[cs.col(mi, ni)] = mul_ipow(mk<float>(re, im), imod(n - m, 4));
     }
   }
   __device__ void zero16(int mp, int mi0, int n0i, int r, int c0) const {
@@ -104,13 +104,13 @@ struct SynthesisProb {
   }
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
     const int mi = mi0 + (r >> 1);
-    const size_t plane = (size_t)cs.Mc * cs.Nc;
+    const cx<float>* plane = Y + (size_t)mp * cs.pitch();
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int ni = k0 + 4 * q + i;
       float v = 0.f;
       if (mi < cs.Mc && ni < cs.Nc) {
-        const cx<float> y = Y[(size_t)mp * plane + (size_t)mi * cs.Nc + ni];
+        const cx<float> y = plane[cs.col(mi, ni)];
         v = (r & 1) ? y.im : y.re;
       }
       x[i] = v;

@@ -19,14 +19,12 @@ struct ColSet {
   int Mc, m0, Nc, n0, nstep;
   int extra;    // added to m+n in parities and phases (spin for the SHT)
   FastDiv fNc;  // division by Nc
-  __device__ __forceinline__ int m_of(int c) const { return m0 + (int)fNc.div((uint32_t)c); }
-  __device__ __forceinline__ int n_of(int c) const { return n0 + nstep * (int)fNc.mod((uint32_t)c); }
-  // parity of m + n + extra for column c
-  __device__ __forceinline__ int par(int c) const {
-    const uint32_t q = fNc.div((uint32_t)c);
-    const int m = m0 + (int)q, n = n0 + nstep * (int)((uint32_t)c - q * (uint32_t)Nc);
-    return (m + n + extra) & 1;
-  }
+  // Column of (mi, ni) in an (m, n) plane: the columns (2i, ni) and (2i + 1, ni) (m and m + 1
+  // at one n, the pairs of the beta transforms) are adjacent, so consecutive pairs fill whole
+  // sectors: c = ((mi / 2) Nc + ni) 2 + mi % 2. A plane holds pitch() columns (one unused
+  // column per n when Mc is odd); with Nc = 1 (the SHT) c = mi.
+  __host__ __device__ __forceinline__ int col(int mi, int ni) const { return (((mi >> 1) * Nc + ni) << 1) | (mi & 1); }
+  __host__ __device__ __forceinline__ size_t pitch() const { return (size_t)((Mc + 1) >> 1) * Nc * 2; }
 };
 
 // L1 prefetch of a global address (no register results): loaders that define
@@ -144,30 +142,34 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
 // the halves separate by that reflection. Pair index p = i * Nc + ni; c_B = -1 if 2i+1 = Mc.
 struct ColPair {
   int cA, cB, parA;  // parA = parity of m + n + extra of column A (B has the other)
+  int mA, n;         // m of column A (B: mA + 1) and n of both
 };
 __device__ __forceinline__ ColPair col_pair(const ColSet& cs, int p) {
   const int i = (int)cs.fNc.div((uint32_t)p), ni = p - i * cs.Nc;
   ColPair r;
-  r.cA = 2 * i * cs.Nc + ni;
-  r.cB = (2 * i + 1 < cs.Mc) ? r.cA + cs.Nc : -1;
-  r.parA = (cs.m0 + cs.n0 + cs.nstep * ni + cs.extra) & 1;
+  r.cA = cs.col(2 * i, ni);
+  r.cB = (2 * i + 1 < cs.Mc) ? r.cA + 1 : -1;
+  r.mA = cs.m0 + 2 * i;
+  r.n = cs.n0 + cs.nstep * ni;
+  r.parA = (r.mA + r.n + cs.extra) & 1;
   return r;
 }
 __host__ __device__ inline int num_col_pairs(const ColSet& cs) { return (cs.Mc + 1) / 2 * cs.Nc; }
 
 
-// Ring inverse, step over n: row (b, mi) of Xb (Nc contiguous) -> T[b][mi][g].
+// Ring inverse, step over n: sequence (b, mi) of the planes Xb[b] -> T[b][mi][g].
 template <class T>
 struct LdRingN {
-  const cx<T>* Xb; int Nc, n0, nstep, N;
+  const cx<T>* Xb; ColSet cs; int N; FastDiv fMc;
   __device__ cx<T> operator()(int c, int j) const {
+    const int b = (int)fMc.div((uint32_t)c), mi = c - b * cs.Mc;
     // j = n mod N; find ni with n0 + nstep*ni == n
     int n = (j <= (N - 1) / 2) ? j : j - N;
-    int d = n - n0;
-    if (d < 0 || (d & (nstep - 1))) return mk<T>(0, 0);
-    const int ni = d >> (nstep - 1);
-    if (ni >= Nc) return mk<T>(0, 0);
-    return Xb[(size_t)c * Nc + ni];
+    int d = n - cs.n0;
+    if (d < 0 || (d & (cs.nstep - 1))) return mk<T>(0, 0);
+    const int ni = d >> (cs.nstep - 1);
+    if (ni >= cs.Nc) return mk<T>(0, 0);
+    return Xb[(size_t)b * cs.pitch() + cs.col(mi, ni)];
   }
 };
 template <class T>
@@ -237,12 +239,12 @@ struct LdRingA {
 };
 template <class T>
 struct StRingA {
-  cx<T>* Xb; int Mc, m0, Nc, N; T scale; FastDiv fNc;
+  cx<T>* Xb; ColSet cs; int N; T scale;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
-    const int b = (int)fNc.div(c), ni = c - b * Nc;
+    const int b = (int)cs.fNc.div((uint32_t)c), ni = c - b * cs.Nc;
     int m = (k <= (N - 1) / 2) ? k : k - N;
-    int mi = m - m0;
-    if (mi >= 0 && mi < Mc) Xb[((size_t)b * Mc + mi) * Nc + ni] = v * scale;
+    int mi = m - cs.m0;
+    if (mi >= 0 && mi < cs.Mc) Xb[(size_t)b * cs.pitch() + cs.col(mi, ni)] = v * scale;
   }
 };
 
@@ -289,12 +291,12 @@ template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 
 // m < 0 by the conjugate of the -n column -> R[b][a][h].
 template <class T>
 struct LdRingMHalf {
-  const cx<T>* Xb; int Mc, Nc, ni0, N, Nh; FastDiv fNh;
+  const cx<T>* Xb; ColSet cs; int ni0, N, Nh; FastDiv fNh;
   __device__ const cx<T>* at(int c, int j, int& m) const {
     const int b = (int)fNh.div((uint32_t)c), ni = ni0 + (c - b * Nh);
     m = (j <= (N - 1) / 2) ? j : j - N;
-    const cx<T>* base = Xb + (size_t)b * Mc * Nc;
-    return m >= 0 ? base + (size_t)m * Nc + ni : base + (size_t)(-m) * Nc + (Nc - 1 - ni);
+    const cx<T>* base = Xb + (size_t)b * cs.pitch();
+    return m >= 0 ? base + cs.col(m, ni) : base + cs.col(-m, cs.Nc - 1 - ni);
   }
   __device__ cx<T> operator()(int c, int j) const {
     int m;
@@ -377,13 +379,13 @@ struct LdRingAHalf {
 };
 template <class T>
 struct StRingAHalf {
-  cx<T>* Xb; int Mc, Nc, ni0, N, Nh; T scale; FastDiv fNh;
+  cx<T>* Xb; ColSet cs; int ni0, N, Nh; T scale; FastDiv fNh;
   __device__ void operator()(int c, int k, cx<T> v, cx<T> vn) const {
-    if (k >= Mc) return;  // m = k >= 0 (Mc = Lb <= (N + 1) / 2)
+    if (k >= cs.Mc) return;  // m = k >= 0 (Mc = Lb <= (N + 1) / 2)
     const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh, ni = ni0 + h;
-    cx<T>* row = Xb + ((size_t)b * Mc + k) * Nc;
-    row[ni] = v * scale;
-    if (h > 0) row[Nc - 1 - ni] = conj(vn) * scale;
+    cx<T>* plane = Xb + (size_t)b * cs.pitch();
+    plane[cs.col(k, ni)] = v * scale;
+    if (h > 0) plane[cs.col(k, cs.Nc - 1 - ni)] = conj(vn) * scale;
   }
 };
 template <class T> struct Mirror<StRingAHalf<T>> { static constexpr int value = 1; };
@@ -543,7 +545,8 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_k
 // This equals the fold Y(m') + (-1)^{m+n+extra} Y(-m') of the full-weight correlation of
 // each column: the odd weights (p = +-1) cancel in that fold, and the even (odd) part of
 // the DFT of a symmetric (antisymmetric) extension is all of it.
-// In: Xb[b][c] (b < Lb); out: Y[m'][c] (m' < Lb). Threads as in dft_kernel with COLS.
+// In: Xb[b][c] (b < Lb, rows of ncols columns); out: Y[m'][c] (m' < Lb). Threads as in
+// dft_kernel with COLS.
 // ---------------------------------------------------------------------------
 template <class T, int NT, int PT>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int Lb,
@@ -601,8 +604,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     }
     __syncthreads();
     if (valid) {
-      const int mA = cs.m_of(cp.cA), n = cs.n_of(cp.cA);
-      const int phA = imod(mA * pa + n * pb + pc, 4), phB = imod((mA + 1) * pa + n * pb + pc, 4);
+      const int phA = imod(cp.mA * pa + cp.n * pb + pc, 4), phB = imod((cp.mA + 1) * pa + cp.n * pb + pc, 4);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int mp = t + q * TP;
