@@ -1,5 +1,6 @@
 """A map's analysis + synthesis through the C ABI captured once in a CUDA graph and replayed
-on new inputs (same buffers) gives the results of the eager calls: the per-call path issues
+on new inputs (same buffers) gives the results of the eager calls (bitwise; the FP64 path's
+synthesis sums with atomics, so there up to summation order): the per-call path issues
 only kernels and asynchronous memsets on the caller's stream (no allocation, no host
 synchronisation), so serving and batching loops can replay it."""
 import os
@@ -50,7 +51,10 @@ def test_round_trip_replays_in_a_cuda_graph(flags):
         m.copy_(torch.from_numpy(maps_h[k][None]))
         g.replay()
         torch.cuda.synchronize()
-        assert torch.equal(out, eager[k][0])
+        if flags & crv.CRV_F_MIXED:
+            assert torch.equal(out, eager[k][0])
+        else:  # the FP64 synthesis accumulates f_lm with atomics: equal up to summation order
+            assert (torch.linalg.norm(out - eager[k][0]) / torch.linalg.norm(eager[k][0])).item() < 1e-13
         for j in range(p.J0, p.J + 1):
             assert torch.equal(W[j], eager[k][1][j])
     crv.crv_plan_check(p.handle)
