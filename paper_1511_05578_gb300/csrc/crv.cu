@@ -773,16 +773,18 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
         base[i] = total - range[i].x;
         total += range[i].y;
       }
-      float* data = p->dalloc<float>((size_t)std::max<long long>(total, 1) * TC_CHUNK_FLOATS, &stt);
+      const size_t nf = (size_t)std::max<long long>(total, 1) * TC_CHUNK_FLOATS;
+      float* hi = p->dalloc<float>(nf, &stt);
+      float* lo = p->dalloc<float>(nf, &stt);
       long long* dbase = p->dalloc<long long>(base.size(), &stt);
       int2* drange = p->dalloc<int2>(range.size(), &stt);
       if (stt != CRV_OK) return stt;
       cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
       cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
       TcTab t;
-      t.data = data; t.base = dbase; t.range = drange; t.ntiles = ntiles;
-      const bool ok = dir == 0 ? tc_fill_analysis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, data, st)
-                               : tc_fill_synthesis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, data, st);
+      t.hi = hi; t.lo = lo; t.base = dbase; t.range = drange; t.ntiles = ntiles;
+      const bool ok = dir == 0 ? tc_fill_analysis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st)
+                               : tc_fill_synthesis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st);
       if (!ok) return CRV_ECUDA;
       (dir == 0 ? p->tabA : p->tabS)[j] = t;
     }
@@ -893,9 +895,10 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->d_err = p->dalloc<int>(1, &stt);
   if (stt == CRV_OK) cudaMemset(p->d_err, 0, sizeof(int));
   {
-    // ring-chunk buffer: at least one ring, at most all rings, about 96 MB (L2-resident)
+    // ring-chunk buffer: at least one ring, at most all rings, 256 MB (larger chunks: fewer
+    // launches; measured 48 -> 120 MB monotonically faster)
     const size_t one = (size_t)(N + 1) * std::max(Mc, Nc) * el;
-    p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)96 << 20));
+    p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)256 << 20));
   }
   p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
   {

@@ -10,9 +10,9 @@
 //
 // Each FP32 operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a K-step issues
 // hi*hi + hi*lo + lo*hi into the same FP32 TMEM accumulator (split-FP32, ~2^-22 per
-// product). The B operand (Delta Psi, independent of the signal) comes from tables
-// built once per plan in the engine's canonical layout; the A operand is built on the
-// fly. See tc_gemm.cuh for the pipeline.
+// product). The B operand (Delta Psi, independent of the signal) comes from tables built
+// once per plan, already split and in the layout of an engine stage, by bulk copies; the A
+// operand is built on the fly. See tc_gemm.cuh for the pipeline.
 #include "tc_contract.cuh"
 #include "tc_gemm.cuh"
 
@@ -25,18 +25,17 @@ static_assert(BNC == TC_TILE_ROWS, "table tiles are accumulator tiles");
 // ---------------------------------------------------------------------------
 // Problems: operand builders, K ranges and epilogues
 // ---------------------------------------------------------------------------
-// Quad q of the K step starting at k0 (a multiple of BK) of row c, from a table chunk of
-// TC_CHUNK_K columns.
-__device__ __forceinline__ void tab4(const TcTab& tb, int mp, int tile, int k0, int c, int q, float* x) {
-  static_assert(TC_CHUNK_K % BK == 0, "engine steps tile the table chunks");
-  const long long chunk = tb.base[mp * tb.ntiles + tile] + k0 / TC_CHUNK_K;
-  const int qq = q + (k0 % TC_CHUNK_K) / 4;
-  const float4 v = __ldg(reinterpret_cast<const float4*>(tb.data + (size_t)chunk * TC_CHUNK_FLOATS + (c >> 3) * 256 +
-                                                         qq * 32 + (c & 7) * 4));
-  x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+// Hi and lo B tiles of the K step starting at k0 (a multiple of BK) for (m', tile).
+__device__ __forceinline__ void tab_tiles(const TcTab& tb, int mp, int tile, int k0, const void*& hi,
+                                          const void*& lo) {
+  static_assert(TC_CHUNK_K == BK, "one table chunk per engine stage");
+  const size_t off = (size_t)(tb.base[mp * tb.ntiles + tile] + k0 / TC_CHUNK_K) * TC_CHUNK_FLOATS;
+  hi = tb.hi + off;
+  lo = tb.lo + off;
 }
 
 struct AnalysisProb {
+  static constexpr bool kBulkB = true;
   const float* Q; int Lmax; const cx<float>* flm; TcTab tb; int Lb; ColSet cs; cx<float>* X;
   // K chunks: the table's run for (m', n-tile), skipping chunks below min |m| of the m-tile
   __device__ void tile(int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
@@ -44,7 +43,7 @@ struct AnalysisProb {
     const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
     const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
     const int2 rg = tb.range[mp * tb.ntiles + blockIdx.x];
-    const int c0 = max(rg.x, amin >> 5), c1 = rg.x + rg.y;
+    const int c0 = max(rg.x, amin / TC_CHUNK_K), c1 = rg.x + rg.y;
     kb = c0 * TC_CHUNK_K;
     ke = max(c0, c1) * TC_CHUNK_K;
   }
@@ -63,7 +62,9 @@ struct AnalysisProb {
       x[i] = v;
     }
   }
-  __device__ void b4(int mp, int n0i, int k0, int c, int q, float* x) const { tab4(tb, mp, n0i / BNC, k0, c, q, x); }
+  __device__ void b_tiles(int mp, int n0i, int k0, const void*& hi, const void*& lo) const {
+    tab_tiles(tb, mp, n0i / BNC, k0, hi, lo);
+  }
   // 16 accumulator columns [c0, c0+16) of row r; lanes r, r^1 hold re/im of the same m
   __device__ void store16(int mp, int mi0, int n0i, int r, int c0, const float* d) const {
     const int mi = mi0 + (r >> 1);
@@ -94,6 +95,7 @@ struct AnalysisProb {
 };
 
 struct SynthesisProb {
+  static constexpr bool kBulkB = true;
   const cx<float>* Y; TcTab tb; int Lb; ColSet cs; cx<float>* Z;
   // K chunks over ni: the table's run for (m', l-tile) (empty if m' > max l of the tile)
   __device__ void tile(int& mp, int& mi0, int& l0, int& kb, int& ke) const {
@@ -116,7 +118,9 @@ struct SynthesisProb {
       x[i] = v;
     }
   }
-  __device__ void b4(int mp, int l0, int k0, int c, int q, float* x) const { tab4(tb, mp, l0 / BNC, k0, c, q, x); }
+  __device__ void b_tiles(int mp, int l0, int k0, const void*& hi, const void*& lo) const {
+    tab_tiles(tb, mp, l0 / BNC, k0, hi, lo);
+  }
   __device__ void store16(int mp, int mi0, int l0, int r, int c0, const float* d) const {
     const int mi = mi0 + (r >> 1);
     const bool odd = r & 1;
@@ -172,18 +176,31 @@ __global__ void __launch_bounds__(256) synth_reduce_kernel(const float* __restri
   f = neg ? f - acc : f + acc;
 }
 
+// Four values as TF32 hi = rna(x) and lo = rna(x - hi) at float offset o of the two tables.
+__device__ __forceinline__ void put_split4(float* hi, float* lo, size_t o, const float* x) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    h[i] = tf32_rna(x[i]);
+    l[i] = tf32_rna(x[i] - __uint_as_float(h[i]));
+  }
+  *reinterpret_cast<uint4*>(hi + o) = make_uint4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint4*>(lo + o) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
 // Table fills: block (tile, m'), thread = row of the 256-row chunks.
 __global__ void __launch_bounds__(256) fill_analysis_table_kernel(const float* __restrict__ Q, int Lmax,
                                                                  const float* __restrict__ psi, int Lb, ColSet cs,
-                                                                 TcTab t, float* __restrict__ data) {
+                                                                 TcTab t, float* __restrict__ hi,
+                                                                 float* __restrict__ lo) {
   const int mp = blockIdx.y, tile = blockIdx.x, r = threadIdx.x;
   const int2 rg = t.range[mp * t.ntiles + tile];
   const long long base = t.base[mp * t.ntiles + tile];
   const int ni = tile * TC_TILE_ROWS + r, n = cs.n0 + cs.nstep * ni, N = 2 * Lb - 1;
   for (int kc = rg.x; kc < rg.x + rg.y; ++kc) {
-    float* chunk = data + (size_t)(base + kc) * TC_CHUNK_FLOATS;
+    const size_t chunk = (size_t)(base + kc) * TC_CHUNK_FLOATS;
 #pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < TC_CHUNK_K / 4; ++q) {
       float v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -192,21 +209,22 @@ __global__ void __launch_bounds__(256) fill_analysis_table_kernel(const float* _
                    ? dq(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)]
                    : 0.f;
       }
-      *reinterpret_cast<float4*>(chunk + (r >> 3) * 256 + q * 32 + (r & 7) * 4) = make_float4(v[0], v[1], v[2], v[3]);
+      put_split4(hi, lo, chunk + (r >> 3) * (TC_CHUNK_K * 8) + q * 32 + (r & 7) * 4, v);
     }
   }
 }
 __global__ void __launch_bounds__(256) fill_synthesis_table_kernel(const float* __restrict__ Q, int Lmax,
                                                                   const float* __restrict__ psi, int Lb, ColSet cs,
-                                                                  TcTab t, float* __restrict__ data) {
+                                                                  TcTab t, float* __restrict__ hi,
+                                                                 float* __restrict__ lo) {
   const int mp = blockIdx.y, tile = blockIdx.x, r = threadIdx.x;
   const int2 rg = t.range[mp * t.ntiles + tile];
   const long long base = t.base[mp * t.ntiles + tile];
   const int l = tile * TC_TILE_ROWS + r, N = 2 * Lb - 1;
   for (int kc = rg.x; kc < rg.x + rg.y; ++kc) {
-    float* chunk = data + (size_t)(base + kc) * TC_CHUNK_FLOATS;
+    const size_t chunk = (size_t)(base + kc) * TC_CHUNK_FLOATS;
 #pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < TC_CHUNK_K / 4; ++q) {
       float v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(256) fill_synthesis_table_kernel(const float* 
                    ? dq(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)]
                    : 0.f;
       }
-      *reinterpret_cast<float4*>(chunk + (r >> 3) * 256 + q * 32 + (r & 7) * 4) = make_float4(v[0], v[1], v[2], v[3]);
+      put_split4(hi, lo, chunk + (r >> 3) * (TC_CHUNK_K * 8) + q * 32 + (r & 7) * 4, v);
     }
   }
 }
@@ -256,20 +274,20 @@ void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int
     }
 }
 
-bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
-                            cudaStream_t st) {
+bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
+                            float* lo, cudaStream_t st) {
   dim3 g(t.ntiles, Lb);
   KTimer kt(K_MISC, st);
-  tc::fill_analysis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, data);
+  tc::fill_analysis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, hi, lo);
   kt.done();
   return launch_ok("fill_analysis_table_kernel");
 }
 
-bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
-                             cudaStream_t st) {
+bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
+                             float* lo, cudaStream_t st) {
   dim3 g(t.ntiles, Lb);
   KTimer kt(K_MISC, st);
-  tc::fill_synthesis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, data);
+  tc::fill_synthesis_table_kernel<<<g, 256, 0, st>>>(Q32, Lmax, psi, Lb, cs, t, hi, lo);
   kt.done();
   return launch_ok("fill_synthesis_table_kernel");
 }

@@ -7,31 +7,33 @@
 
 namespace crv {
 
-// Plan-constant B operand of one contraction and one scale: for every (m', tile) the run
-// of 32-wide K chunks that the tile multiplies, each chunk a 256-row x 32 FP32 block in
-// the canonical K-major layout of the tensor-core engine (rows in 8-row groups of 1 KB,
-// k-quads 128 B apart, 16 B per row and quad).
+// Plan-constant B operand of one contraction and one scale: for every (m', tile) the run of
+// 16-wide K chunks that the tile multiplies, each chunk a 256-row x 16 block in exactly the
+// shared-memory layout of one stage of the tensor-core engine (rows in 8-row groups of 512 B,
+// k-quads 128 B apart, 16 B per row and quad), already split into TF32 hi = rna(x) and
+// lo = rna(x - hi), so that one bulk copy per half fills a stage.
 //   analysis:  rows n (256 per tile), K = l,  value Delta^l_{m'n} Psi_ln
 //   synthesis: rows l (256 per tile), K = ni, value Delta^l_{m'n} Psi_ln
-// Chunk kc of (m', tile) sits at data + (base[m' * ntiles + tile] + kc) * 8192;
-// range[m' * ntiles + tile] = (first chunk, number of chunks); entries outside the
-// support (l < max(m', |n|), l >= Lb, ni >= Nc) are zero.
+// Chunk kc of (m', tile) sits at hi/lo + (base[m' * ntiles + tile] + kc) * TC_CHUNK_FLOATS;
+// range[m' * ntiles + tile] = (first chunk, number of chunks); entries outside the support
+// (l < max(m', |n|), l >= Lb, ni >= Nc) are zero.
 struct TcTab {
-  const float* data = nullptr;
+  const float* hi = nullptr;
+  const float* lo = nullptr;
   const long long* base = nullptr;
   const int2* range = nullptr;
   int ntiles = 0;
 };
-constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 32, TC_CHUNK_FLOATS = TC_TILE_ROWS * TC_CHUNK_K;
+constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 16, TC_CHUNK_FLOATS = TC_TILE_ROWS * TC_CHUNK_K;
 
 // Chunk ranges per (m', tile), m' < Lb (host).
 void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
 void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
 // Fill a table (device); t.base / t.range already on the device.
-bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
-                            cudaStream_t st);
-bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* data,
-                             cudaStream_t st);
+bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
+                            float* lo, cudaStream_t st);
+bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
+                             float* lo, cudaStream_t st);
 
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
                  int* err, cudaStream_t st);

@@ -12,6 +12,7 @@
 // overlap the other's MMAs.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "transforms.cuh"
 
@@ -28,7 +29,7 @@ template <int BN>
 struct Geo {
   static constexpr int B_BYTES = BN * BK * 4;                       // B tile (hi or lo)
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2048;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2048;  // + alignment slack and barriers
   static constexpr int TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
   // instruction descriptor: D f32, A/B tf32, K-major A and B, N = BN, M = 128
   static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -75,6 +76,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicExch(err, 1);
   return false;
+}
+// Arm an mbarrier for one arrival carrying tx bytes of asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bulk copy global -> shared (16-byte aligned, multiple of 16 bytes) completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -126,10 +138,16 @@ __device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a
 // The GEMM kernel: one 128 x BN output tile per CTA.
 //   Prob::tile(z, r0, c0, kb, ke)             tile coordinates and K range from blockIdx
 //   Prob::a4(z, r0, k0, r, q, x[4])           A[r0 + r][k0 + 4q .. +3]
-//   Prob::b4(z, c0, k0, c, q, x[4])           B[c0 + c][k0 + 4q .. +3]
 //   Prob::store16(z, r0, c0, r, cc, d[16])    D[r0 + r][c0 + cc .. +15] (all 32 lanes call it)
 //   Prob::zero16(z, r0, c0, r, cc)            same for a tile with an empty K range
+// and for B either (Prob::kBulkB false)
+//   Prob::b4(z, c0, k0, c, q, x[4])           B[c0 + c][k0 + 4q .. +3], split by the threads
+// or (Prob::kBulkB true) the stage's B tiles already split and laid out, copied by one thread
+// with cp.async.bulk on the stage's full barrier:
+//   Prob::b_tiles(z, c0, k0, hi, lo)          device addresses of the hi and lo tiles (B_BYTES each)
 // ---------------------------------------------------------------------------
+template <class P, class = void> struct BulkB { static constexpr bool value = false; };
+template <class P> struct BulkB<P, std::enable_if_t<P::kBulkB>> { static constexpr bool value = true; };
 template <class Prob, int BN>
 __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   using G = Geo<BN>;
@@ -137,8 +155,10 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   extern __shared__ unsigned char smraw[];
   const uint32_t raw = smem_u32(smraw);
   unsigned char* base = smraw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned stage buffers
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
+  constexpr bool BULK = BulkB<Prob>::value;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // MMAs of the stage done
+  uint64_t* full = bars + STAGES;                                             // B copies of the stage landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + STAGES);
   const int tid = threadIdx.x, warp = tid >> 5;
 
   int mp, r0, c0g, kb, ke;
@@ -146,7 +166,10 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   const int nchunks = (ke > kb) ? (ke - kb + BK - 1) / BK : 0;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s]);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&bars[s]);
+      mbar_init(&full[s]);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -161,10 +184,12 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
+  uint32_t pend = 0;      // thread 0: stages with B copies in flight (bit s), issued at chunk pend_c[s]
+  int pend_c[STAGES];
   // Operand quads of one K chunk per thread: A 128 rows x BK/4 k-quads, B BN rows x BK/4.
   // The loads of chunk c + 1 are issued as soon as chunk c is in shared memory, so their
   // latency overlaps the barrier and the MMAs of chunk c.
-  constexpr int NA = BM * (BK / 4) / NT, NB = BN * (BK / 4) / NT;
+  constexpr int NA = BM * (BK / 4) / NT, NB = BULK ? 1 : BN * (BK / 4) / NT;
   float xa[NA][4], xb[NB][4];
   auto load_chunk = [&](int c) {
     const int k0 = kb + c * BK;
@@ -173,12 +198,29 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       const int it = tid + i * NT;
       pb.a4(mp, r0, k0, it % BM, it / BM, xa[i]);
     }
+    if constexpr (!BULK) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const int it = tid + i * NT;
-      pb.b4(mp, c0g, k0, it % BN, it / BN, xb[i]);
+      for (int i = 0; i < NB; ++i) {
+        const int it = tid + i * NT;
+        pb.b4(mp, c0g, k0, it % BN, it / BN, xb[i]);
+      }
     }
   };
+  // thread 0: bulk copies of chunk c's B tiles into its stage, completing on full[stage]
+  auto issue_b = [&](int c) {
+    const int sc = c % STAGES;
+    unsigned char* stc = base + sc * STAGE_BYTES;
+    const void *bhi, *blo;
+    pb.b_tiles(mp, c0g, kb + c * BK, bhi, blo);
+    mbar_expect_tx(&full[sc], 2u * B_BYTES);
+    bulk_g2s(stc + 2 * A_BYTES, bhi, B_BYTES, &full[sc]);
+    bulk_g2s(stc + 2 * A_BYTES + B_BYTES, blo, B_BYTES, &full[sc]);
+    pend |= 1u << sc;
+    pend_c[sc] = c;
+  };
+  if constexpr (BULK) {
+    if (tid == 0 && nchunks > 0) issue_b(0);
+  }
   if (nchunks > 0) load_chunk(0);
   for (int c = 0; c < nchunks; ++c) {
     const int s = c % STAGES;
@@ -189,14 +231,22 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       const int it = tid + i * NT;
       put4(st, st + A_BYTES, it % BM, it / BM, xa[i]);
     }
+    if constexpr (!BULK) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const int it = tid + i * NT;
-      put4(st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, it % BN, it / BN, xb[i]);
+      for (int i = 0; i < NB; ++i) {
+        const int it = tid + i * NT;
+        put4(st + 2 * A_BYTES, st + 2 * A_BYTES + B_BYTES, it % BN, it / BN, xb[i]);
+      }
     }
     if (c + 1 < nchunks) load_chunk(c + 1);
     fence_proxy_async();
     __syncthreads();
+    if constexpr (BULK) {
+      if (tid == 0 && (pend & (1u << s))) {
+        ok = mbar_wait(&full[s], (uint32_t)(c / STAGES) & 1u, err) && ok;
+        if (ok) pend &= ~(1u << s);
+      }
+    }
     if (tid == 0 && ok) {
       fence_after();
       const uint32_t sa = smem_u32(st);
@@ -212,10 +262,24 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       }
       mma_commit(&bars[s]);
     }
+    if constexpr (BULK) {
+      // B tiles of chunk c + 1 into the other stage once its MMAs (chunk c - 1) are done, so
+      // the copies overlap the next iteration's A build
+      if (tid == 0 && ok && c + 1 < nchunks) {
+        const int s1 = (c + 1) % STAGES;
+        if (c + 1 >= STAGES) ok = mbar_wait(&bars[s1], (uint32_t)(((c + 1) / STAGES) - 1) & 1u, err) && ok;
+        if (ok) issue_b(c + 1);
+      }
+    }
   }
   if (nchunks > 0) {
     const int last = nchunks - 1;
     ok = mbar_wait(&bars[last % STAGES], (uint32_t)(last / STAGES) & 1u, err) && ok;
+  }
+  if constexpr (BULK) {  // a wait that gave up may leave copies in flight: let them land first
+    if (tid == 0)
+      for (int s = 0; s < STAGES; ++s)
+        if (pend & (1u << s)) mbar_wait(&full[s], (uint32_t)(pend_c[s] / STAGES) & 1u, err);
   }
   fence_after();
   // Epilogue on all warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lanes it may
