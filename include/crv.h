@@ -68,7 +68,14 @@ enum {
   CRV_F_REAL = 1,   /* spin-0 real signal: real maps and real W (conjugate symmetry, Sec. III-A-3) */
   CRV_F_MIXED = 2,  /* split-FP32 contraction on tensor cores and FP32 FFTs; Delta recursion
                        and the synthesis accumulation of f_lm stay FP64 */
-  CRV_F_W_FP32 = 4  /* store W_j as float instead of double */
+  CRV_F_W_FP32 = 4, /* store W_j as float instead of double */
+  CRV_F_UNROTATED = 8 /* W_j are the coefficients of the unrotated curvelets s-psi~^(j) (Sec. III-A-1),
+                         i.e. W~(rho) with W(rho) = W~(rho rho*), rho* = (0, vartheta^j, 0) (Eq.
+                         rotateWigner). Their Wigner coefficients vanish unless |n| = l (Eq.
+                         curvelet_Wigner_property), so Eq. inverse_Fmnmp keeps the one term l = |n|
+                         and the Delta contraction costs O(L^3) instead of O(L^4) per scale (the
+                         paper's own fast algorithm); the synthesis keeps n = +-l of Eq. flml.
+                         Same grids, sizes and layouts as the rotated W_j. */
 };
 
 /* Create a plan.
@@ -83,7 +90,8 @@ enum {
  *             only bounds argument checks)
  *   stream    CUDA stream used for the table build (Delta recursion)
  * Builds the radial kernels kappa^(j) and scaling function (Sec. II-B), the rotated
- * directional components zeta^(j) (Eq. after directionality_normalisation), the
+ * directional components zeta^(j) (Eq. after directionality_normalisation; with
+ * CRV_F_UNROTATED the unrotated zeta~ with zeta~_{l,l} = 1/sqrt2, zeta~_{l,-l} = (-1)^l/sqrt2), the
  * Delta^l = d^l(pi/2) tables (FP64, on the device), FFT tables and workspace.
  * Synchronises the stream. On error *out is NULL. */
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule,

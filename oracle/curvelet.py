@@ -16,8 +16,8 @@ from . import build as _build
 __all__ = [
     "lib", "mw_theta", "mw_phi", "half_angles", "wigner_d_factsum", "wigner_d_lrec",
     "risbo_matrix", "delta_matrix", "quad_weight", "sht_inverse", "sht_forward",
-    "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "psi",
-    "analysis_rings", "analysis_from_flm", "analysis", "scaling_map", "wigner_forward_Y",
+    "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "zeta_unrotated", "psi",
+    "euler_matrix", "euler_angles", "analysis_point", "analysis_rings", "analysis_from_flm", "analysis", "scaling_map", "wigner_forward_Y",
     "wigner_forward_coeffs", "synthesis_flm", "synthesis", "MUTATION",
 ]
 
@@ -264,28 +264,79 @@ def zeta(lam, j, s, Lj):
     return out
 
 
-def psi(lam, j, s, Lj):
+def zeta_unrotated(s, Lj):
+    """Directional component of the unrotated curvelets s-psi~ (Sec. II-B, printed
+    definition read with delta_{l|m|}): zeta~_{l,l} = 1/sqrt2, zeta~_{l,-l} =
+    (-1)^l/sqrt2, zeta~_00 = 1/sqrt2; zero for l < |s|. Returns [Lj][2Lj-1] (real)."""
+    out = np.zeros((Lj, 2 * Lj - 1))
+    for l in range(abs(s), Lj):
+        out[l, Lj - 1 + l] = 1.0 / math.sqrt(2)
+        if l > 0:
+            out[l, Lj - 1 - l] = (-1) ** l / math.sqrt(2)
+    return out
+
+
+def psi(lam, j, s, Lj, unrotated=False):
     """Curvelet harmonic coefficients sPsi^(j)_ln = sqrt((2l+1)/8pi^2) kappa^(j)(l) zeta_ln
-    (Eq. wav_factorized), [Lj][2Lj-1], real."""
+    (Eq. wav_factorized), [Lj][2Lj-1], real; with unrotated=True those of s-psi~^(j),
+    with zeta~ in place of zeta (nonzero for |n| = l only)."""
     l = np.arange(Lj, dtype=np.float64)
     fac = np.sqrt((2 * l + 1) / (8 * np.pi ** 2)) * kappa(lam, j, Lj)
-    return np.ascontiguousarray(fac[:, None] * zeta(lam, j, s, Lj))
+    z = zeta_unrotated(s, Lj) if unrotated else zeta(lam, j, s, Lj)
+    return np.ascontiguousarray(fac[:, None] * z)
+
+
+def euler_matrix(alpha, beta, gamma):
+    """Rotation R(alpha, beta, gamma) = R_z(alpha) R_y(beta) R_z(gamma) of R^3, the
+    rotation whose Wigner matrix is D^l_mn = e^{-i m alpha} d^l_mn(beta) e^{-i n gamma}."""
+    def rz(t):
+        c, s_ = math.cos(t), math.sin(t)
+        return np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+
+    def ry(t):
+        c, s_ = math.cos(t), math.sin(t)
+        return np.array([[c, 0.0, s_], [0.0, 1.0, 0.0], [-s_, 0.0, c]])
+    return rz(alpha) @ ry(beta) @ rz(gamma)
+
+
+def euler_angles(R):
+    """(alpha, beta, gamma) of a rotation matrix in the convention of euler_matrix
+    (beta in [0, pi]; generic rotations, sin beta != 0)."""
+    beta = math.acos(max(-1.0, min(1.0, R[2, 2])))
+    alpha = math.atan2(R[1, 2], R[0, 2])
+    gamma = math.atan2(R[2, 1], -R[2, 0])
+    return alpha, beta, gamma
+
+
+def analysis_point(flm, psi_j, Lj, alpha, beta, gamma):
+    """W(rho) at one arbitrary rotation rho = (alpha, beta, gamma) by the direct sum of
+    Eq. (wav_analysis_harmonic), D^{l*}_mn = e^{i m alpha} d^l_mn(beta) e^{i n gamma},
+    d from the factorial sum. Tiny Lj only."""
+    acc = 0j
+    for l in range(Lj):
+        for m in range(-l, l + 1):
+            for n in range(-l, l + 1):
+                c = flm[l * l + l + m] * psi_j[l, n + Lj - 1]
+                if c != 0:
+                    acc += c * wigner_d_factsum(l, m, n, beta) * np.exp(1j * (m * alpha + n * gamma))
+    return acc
 
 
 # --------------------------------------------------------------------------
 # Curvelet analysis (Sec. II-D-1)
 # --------------------------------------------------------------------------
-def analysis_rings(flm, lam, j, s, L, rings=None, psi_j=None, method="risbo"):
+def analysis_rings(flm, lam, j, s, L, rings=None, psi_j=None, method="risbo", unrotated=False):
     """W^(j)(alpha_a, beta_b, gamma_g) at the requested rings b, by direct evaluation
     of Eq. (wav_analysis_harmonic) with D^{l*}_mn = e^{i m a} d^l_mn(b) e^{i n g};
     d^l(beta_b) by Risbo's recursion at beta_b (method="risbo") or by the
-    l-recurrence ("lrec"). Returns complex [len(rings)][2Lj-1 (a)][2Lj-1 (g)]."""
+    l-recurrence ("lrec"). unrotated=True: W~ of the unrotated curvelets.
+    Returns complex [len(rings)][2Lj-1 (a)][2Lj-1 (g)]."""
     Lj = band_limit(lam, j, L)
     N = 2 * Lj - 1
     if rings is None:
         rings = range(Lj)
     rings = list(rings)
-    ps = psi(lam, j, s, Lj) if psi_j is None else psi_j
+    ps = psi(lam, j, s, Lj, unrotated) if psi_j is None else psi_j
     f = np.ascontiguousarray(np.asarray(flm, dtype=np.complex128)[: Lj * Lj])
     out = np.empty((len(rings), N, N), dtype=np.complex128)
     X = np.empty((N, N), dtype=np.complex128)
@@ -309,18 +360,19 @@ def scaling_map(flm, lam, J0, L):
     return sht_inverse(c, Lp, 0)
 
 
-def analysis_from_flm(flm, lam, J0, s, L, rings=None):
+def analysis_from_flm(flm, lam, J0, s, L, rings=None, unrotated=False):
     J = J_max(lam, L)
     W = {}
     for j in range(J0, J + 1):
-        W[j] = analysis_rings(flm, lam, j, s, L, None if rings is None else rings.get(j, None))
+        W[j] = analysis_rings(flm, lam, j, s, L, None if rings is None else rings.get(j, None), unrotated=unrotated)
     return W, scaling_map(flm, lam, J0, L)
 
 
-def analysis(fmap, lam, J0, s, L, rings=None):
-    """Curvelet analysis of a map: (f_lm, {W_j}, W^Phi)."""
+def analysis(fmap, lam, J0, s, L, rings=None, unrotated=False):
+    """Curvelet analysis of a map: (f_lm, {W_j}, W^Phi); unrotated=True gives the W~_j of
+    the unrotated curvelets (the scaling map is the same)."""
     flm = sht_forward(fmap, L, s)
-    W, Wphi = analysis_from_flm(flm, lam, J0, s, L, rings)
+    W, Wphi = analysis_from_flm(flm, lam, J0, s, L, rings, unrotated)
     return flm, W, Wphi
 
 
@@ -350,9 +402,10 @@ def wigner_forward_coeffs(Wj, Lj):
     return wl
 
 
-def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None):
+def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None, unrotated=False):
     """f_lm from curvelet and scaling coefficients, Eq. (wav_synthesis_harmonic).
-    W maps scale j -> [Lj][2Lj-1][2Lj-1]; scales missing from W contribute nothing."""
+    W maps scale j -> [Lj][2Lj-1][2Lj-1]; scales missing from W contribute nothing.
+    unrotated=True: W holds the W~_j of the unrotated curvelets."""
     J = J_max(lam, L)
     f = np.zeros(L * L, dtype=np.complex128)
     for j in range(J0, J + 1):
@@ -360,7 +413,7 @@ def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None):
             continue
         Lj = band_limit(lam, j, L)
         Y = wigner_forward_Y(W[j], Lj)
-        ps = psi(lam, j, s, Lj)
+        ps = psi(lam, j, s, Lj, unrotated)
         part = np.zeros(Lj * Lj, dtype=np.complex128)
         lib().orc_wigner_fwd_contract(Lj, _p(Y.view(np.float64)), _p(ps), _p(part.view(np.float64)), None)
         f[: Lj * Lj] += part
@@ -374,6 +427,6 @@ def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None):
     return f
 
 
-def synthesis(W, Wphi, lam, J0, s, L):
+def synthesis(W, Wphi, lam, J0, s, L, unrotated=False):
     """Curvelet synthesis back to the MW map (complex [L][2L-1])."""
-    return sht_inverse(synthesis_flm(W, Wphi, lam, J0, s, L), L, s)
+    return sht_inverse(synthesis_flm(W, Wphi, lam, J0, s, L, unrotated=unrotated), L, s)
