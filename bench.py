@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--lam", type=float, default=2.0)
     ap.add_argument("--J0", type=int, default=2)
     ap.add_argument("--mode", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--unrotated", action="store_true",
+                    help="coefficients of the unrotated curvelets (CRV_F_UNROTATED: single-term l = |n| contraction)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -108,7 +110,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic work per map (for the roofline object)
 # ---------------------------------------------------------------------------
-def plan_shapes(L, lam, J0, real=True, spin=0):
+def plan_shapes(L, lam, J0, real=True, spin=0, unrot=False):
     J = 0
     while lam ** J < L * (1 - 1e-14):
         J += 1
@@ -119,7 +121,7 @@ def plan_shapes(L, lam, J0, real=True, spin=0):
         Lb = min(L, int(r) if abs(v - r) < 1e-9 * max(1, v) else int(math.ceil(v)))
         N = 2 * Lb - 1
         Mc = Lb if real else N
-        if spin == 0:
+        if spin == 0 and not unrot:
             n0 = -(Lb - 1) + ((Lb - 1) % 2)
             Nc = (-n0 - n0) // 2 + 1
         else:
@@ -143,12 +145,12 @@ def fft_flops(n):
     return 5.0 * n * math.log2(n) if n > 1 else 0.0
 
 
-def kind_work(L, lam, J0, el_bytes, w_bytes):
+def kind_work(L, lam, J0, el_bytes, w_bytes, unrot=False):
     """Algorithmic bytes (input read + output written, once) and flops per map for each
     kernel kind of the Wigner pipelines. DFT flops use the conventional 5 N log2 N per
     complex length-N transform (half that for a real-input or real-output one); the
     beta quadrature adds its weight correlation as two length-Q transforms."""
-    J, shapes = plan_shapes(L, lam, J0)
+    J, shapes = plan_shapes(L, lam, J0, unrot=unrot)
     w = {}
 
     def add(k, b=0.0, f=0.0):
@@ -159,6 +161,9 @@ def kind_work(L, lam, J0, el_bytes, w_bytes):
         wv = Lb * N * N * w_bytes               # W_j
         terms = contraction_terms(Lb)
         Q = 1 << max(3, (4 * Lb - 4).bit_length())
+        if unrot:
+            # single term l = |n|: the volume is written (analysis) or read (synthesis) once
+            terms = Lb * Lb * Lb
         add("contract_analysis", vol, 4.0 * terms)
         add("tc_analysis", vol, 4.0 * terms)
         Nh = (Nc + 1) // 2                      # columns n >= 0 (real signals: F_{-m,-n} = conj F_{m,n})
@@ -221,7 +226,7 @@ def fp64_alu_peak_tflops(sm_mhz):
 # ---------------------------------------------------------------------------
 # the oracle arm (CPU)
 # ---------------------------------------------------------------------------
-def oracle_maps_per_s(L, lam, J0, rings_per_sample=1, seed=2000):
+def oracle_maps_per_s(L, lam, J0, rings_per_sample=1, seed=2000, unrot=False):
     """Time the FP64 oracle's curvelet analysis on sampled rings of the top scale and
     extrapolate to one full map round trip: analysis cost per ring scales as L_j^3
     (Risbo recursion at beta_b plus the per-ring sums), summed over all rings of all
@@ -233,7 +238,7 @@ def oracle_maps_per_s(L, lam, J0, rings_per_sample=1, seed=2000):
     f = inputs.flm_gaussian(L, seed, real=True)
     J = O.J_max(lam, L)
     Lt = O.band_limit(lam, J, L)
-    ps = O.psi(lam, J, 0, Lt)
+    ps = O.psi(lam, J, 0, Lt, unrot)
     rings = list(np.linspace(0, Lt - 1, rings_per_sample + 2).astype(int)[1:-1])
     t0 = time.perf_counter()
     O.analysis_rings(f, lam, J, 0, L, rings=rings, psi_j=ps)
@@ -260,9 +265,9 @@ def run_reference(args, rank, world):
     vals = []
     rings = 4  # ~2-3 s of oracle work per step on 16 host cores at L = 1024
     for _ in range(args.warmup):
-        oracle_maps_per_s(args.L, args.lam, args.J0, 1)
+        oracle_maps_per_s(args.L, args.lam, args.J0, 1, unrot=args.unrotated)
     for _ in range(args.steps):
-        v, info = oracle_maps_per_s(args.L, args.lam, args.J0, rings)
+        v, info = oracle_maps_per_s(args.L, args.lam, args.J0, rings, unrot=args.unrotated)
         vals.append(v)
     v = sorted(vals)[len(vals) // 2]
     sample = (f"{rings} rings of the top scale (L_j={args.L}) per step, extrapolated by L_j^3 over all rings of "
@@ -280,9 +285,10 @@ def run_reference(args, rank, world):
 
 def config_dict(args):
     return {"workload": f"curvelet analysis+synthesis, {args.B} real spin-0 maps, L={args.L}, lambda={args.lam:g}, "
-                        f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}",
+                        f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}"
+                        + (", unrotated curvelets (O(L^3) single-term contraction)" if args.unrotated else ""),
             "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
-            "precision": args.mode, "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)"}
+            "precision": args.mode, "unrotated": bool(args.unrotated), "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)"}
 
 
 # ---------------------------------------------------------------------------
@@ -309,6 +315,8 @@ def main():
     build.build()
     L, lam, J0, B = args.L, args.lam, args.J0, args.B
     flags = crv.CRV_F_REAL | (crv.CRV_F_MIXED | crv.CRV_F_W_FP32 if args.mode == "mixed" else 0)
+    unrot_flag = crv.CRV_F_UNROTATED if args.unrotated else 0
+    flags |= unrot_flag
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         plan = crv.Plan(L, lam, J0, 0, flags, max_batch=1, stream=stream.cuda_stream)
@@ -419,7 +427,7 @@ def main():
         del W
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
-            p64 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL, max_batch=1, stream=stream.cuda_stream)
+            p64 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL | unrot_flag, max_batch=1, stream=stream.cuda_stream)
             W64 = p64.W_tensors(1)
             P64 = p64.Wphi_tensor(1)
             o64 = torch.empty_like(maps[:1])
@@ -443,7 +451,7 @@ def main():
     peaks = measured_peaks()
     el = 8 if args.mode == "mixed" else 16
     wb = 4 if args.mode == "mixed" else 8
-    work = kind_work(L, lam, J0, el, wb)
+    work = kind_work(L, lam, J0, el, wb, args.unrotated)
     dom = max(kind_ms, key=kind_ms.get) if kind_ms else None
     roof = None
     if dom:
@@ -489,7 +497,7 @@ def main():
         "kernels_ms_per_step": {k: v / args.steps for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, info = oracle_maps_per_s(L, lam, J0, 20)  # ~10-15 s of oracle work on 16 host cores
+        v, info = oracle_maps_per_s(L, lam, J0, 20, unrot=args.unrotated)  # ~10-15 s of oracle work on 16 host cores
         line["cpu_baseline"] = {"value": v, "unit": "maps/s", "cores": cpu_cores(), "kind": "oracle",
                                 "sample": f"FP64 oracle analysis of {info['rings']} rings of the top scale (L_j={L}, "
                                           f"{info['ring_s']:.2f} s per ring), extrapolated by L_j^3 over all rings of "

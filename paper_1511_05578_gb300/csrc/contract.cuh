@@ -201,6 +201,157 @@ __global__ void __launch_bounds__(256) contract_synthesis_kernel(const T* __rest
 }
 
 // ---------------------------------------------------------------------------
+// Unrotated curvelets (Sec. III-A-1, plans with CRV_F_UNROTATED). The Wigner coefficients
+// of W~ vanish unless |n| = l (Eq. curvelet_Wigner_property), so each Delta contraction
+// keeps a single term:
+//   analysis  (Eq. inverse_Fmnmp):    X_{m n m'} = i^{n-m} Delta^{|n|}_{m'm} Delta^{|n|}_{m'n} f_{|n| m} Psi~_{|n| n}
+//   synthesis (Eq. flml with n = +-l): f_lm += sum_{m'>=0} Delta^l_{m'm} sum_{n=+-l} Delta^l_{m'n} Psi~_ln Y'_{m n m'}
+// (Y' carries i^{m-n}), O(L^3) per scale and bound by the volume traffic. The planes hold
+// every n (nstep = 1), pair-interleaved as everywhere.
+// ---------------------------------------------------------------------------
+constexpr int UA_PAIRS = 8, UA_N = 64;
+
+// One (m, n) plane m' = blockIdx.z; a block covers UA_PAIRS column pairs (m, m+1) x UA_N
+// values of n. Phase 1 forms the products with m fastest (coalesced rows Q[m'][l][|m|] and
+// f_lm); phase 2 writes them in column order (per pair row, 2 UA_N contiguous columns).
+// Every column of the plane is written, zeros included (the odd-Mc padding column too).
+// grid = (ceil(Nc / UA_N), ceil(ceil(Mc/2) / UA_PAIRS), Lb).
+template <class T>
+__global__ void __launch_bounds__(256) unrot_analysis_kernel(const T* __restrict__ Q, int Lmax,
+                                                             const cx<double>* __restrict__ flm,
+                                                             const T* __restrict__ psi, int Lb, ColSet cs,
+                                                             cx<T>* __restrict__ X) {
+  __shared__ cx<T> S[UA_N][2 * UA_PAIRS + 1];
+  const int N = 2 * Lb - 1, mp = blockIdx.z;
+  const int pi0 = blockIdx.y * UA_PAIRS, mi0 = 2 * pi0, ni0 = blockIdx.x * UA_N;
+  for (int e = threadIdx.x; e < UA_N * 2 * UA_PAIRS; e += blockDim.x) {
+    const int nl = e / (2 * UA_PAIRS), ml = e % (2 * UA_PAIRS);
+    const int mi = mi0 + ml, ni = ni0 + nl;
+    cx<T> v = mk<T>(0, 0);
+    if (mi < cs.Mc && ni < cs.Nc) {
+      const int m = cs.m0 + mi, n = cs.n0 + ni;
+      const int l = n < 0 ? -n : n, am = m < 0 ? -m : m;
+      if (l >= am && l >= mp) {
+        const T ps = psi[(size_t)l * N + (n + Lb - 1)];
+        if (ps != (T)0) {
+          const T d = delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, n) * ps;
+          const cx<double> f = flm[l * l + l + m];
+          v = mul_ipow(mk<T>(d * (T)f.re, d * (T)f.im), imod(n - m, 4));
+        }
+      }
+    }
+    S[nl][ml] = v;
+  }
+  __syncthreads();
+  const int npairs = (cs.Mc + 1) >> 1;
+  cx<T>* plane = X + (size_t)mp * cs.pitch();
+  for (int e = threadIdx.x; e < UA_PAIRS * 2 * UA_N; e += blockDim.x) {
+    const int r = e / (2 * UA_N), w = e % (2 * UA_N), nl = w >> 1, par = w & 1;
+    const int ni = ni0 + nl;
+    if (pi0 + r >= npairs || ni >= cs.Nc) continue;
+    plane[((size_t)(pi0 + r) * cs.Nc + ni) * 2 + par] = S[nl][2 * r + par];
+  }
+}
+
+constexpr int US_L = 32, US_PAIRS = 8, US_MPC = 128;
+
+// Synthesis: a block covers US_L values of l (both n = +l and n = -l) x US_PAIRS column
+// pairs and a chunk of US_MPC values of m'. Per m' the rows Delta^l_{m'm} of the tile pass
+// through shared memory (loaded m fastest), the Y' columns are read in column order; thread
+// slot k holds n = +l and slot k + 2 the same (l, m) with n = -l. Products are summed in T,
+// flushed to FP64 every 32 m'; the chunk's sums go to P[chunk][l*l + l + m] for every l < Lb,
+// m in the m-set, |m| <= l (zeros included), and unrot_reduce_kernel adds the chunks in order.
+// grid = (ceil(Lb / US_L), ceil(ceil(Mc/2) / US_PAIRS), ceil(Lb / US_MPC)).
+template <class T>
+__global__ void __launch_bounds__(256) unrot_synthesis_kernel(const T* __restrict__ Q, int Lmax,
+                                                              const cx<T>* __restrict__ Y,
+                                                              const T* __restrict__ psi, int Lb, ColSet cs,
+                                                              cx<double>* __restrict__ P) {
+  __shared__ T Dm[2][US_L][2 * US_PAIRS + 1];  // Delta^l_{m'm}
+  __shared__ T Dn[2][2][US_L];                  // Delta^l_{m',+-l} Psi~_{l,+-l}
+  const int N = 2 * Lb - 1;
+  const int l0 = blockIdx.x * US_L, pi0 = blockIdx.y * US_PAIRS, mi0 = 2 * pi0;
+  const int mp0 = blockIdx.z * US_MPC;
+  const int lhi = min(l0 + US_L, Lb) - 1;
+  const int mp1 = min(mp0 + US_MPC, lhi + 1);
+  const size_t pitch = cs.pitch();
+  const int t = threadIdx.x;
+  // the thread's four slots: e = t + 256 k -> (sign, pair row r, l, parity)
+  size_t col[4];
+  int ll[4], ml[4];
+  bool ok[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int e = t + 256 * k, sg = e / (US_PAIRS * 2 * US_L), r = (e / (2 * US_L)) % US_PAIRS, w = e % (2 * US_L);
+    ll[k] = w >> 1;
+    ml[k] = 2 * r + (w & 1);
+    const int l = l0 + ll[k], mi = mi0 + ml[k], m = cs.m0 + mi;
+    const int n = sg ? -l : l;
+    ok[k] = l < Lb && mi < cs.Mc && (m < 0 ? -m : m) <= l && !(sg && l == 0);
+    col[k] = ok[k] ? ((size_t)(pi0 + r) * cs.Nc + (n - cs.n0)) * 2 + (w & 1) : 0;
+  }
+  cx<double> acc[4];
+  cx<T> part[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { acc[k] = mk(0.0, 0.0); part[k] = mk<T>(0, 0); }
+  for (int mp = mp0; mp < mp1; ++mp) {
+    const int bf = mp & 1;
+    for (int e = t; e < US_L * 2 * US_PAIRS; e += 256) {
+      const int a = e / (2 * US_PAIRS), b = e % (2 * US_PAIRS);
+      const int l = l0 + a, mi = mi0 + b, m = cs.m0 + mi;
+      T d = 0;
+      if (l < Lb && l >= mp && mi < cs.Mc && (m < 0 ? -m : m) <= l) d = delta_q(Q, Lmax, mp, l, m);
+      Dm[bf][a][b] = d;
+    }
+    if (t < 2 * US_L) {
+      const int sg = t / US_L, a = t % US_L, l = l0 + a, n = sg ? -l : l;
+      T d = 0;
+      if (l < Lb && l >= mp) d = delta_q(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)];
+      Dn[bf][sg][a] = d;
+    }
+    __syncthreads();
+    const cx<T>* Yp = Y + (size_t)mp * pitch;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (!ok[k]) continue;
+      const cx<T> y = Yp[col[k]];
+      const T c = Dm[bf][ll[k]][ml[k]] * Dn[bf][k >> 1][ll[k]];
+      part[k].re += c * y.re;
+      part[k].im += c * y.im;
+    }
+    if (((mp - mp0) & 31) == 31) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        acc[k].re += (double)part[k].re; acc[k].im += (double)part[k].im;
+        part[k] = mk<T>(0, 0);
+      }
+    }
+  }
+  const int cidx = blockIdx.z;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    acc[k].re += (double)part[k].re + (double)part[k + 2].re + acc[k + 2].re;
+    acc[k].im += (double)part[k].im + (double)part[k + 2].im + acc[k + 2].im;
+    const int l = l0 + ll[k], mi = mi0 + ml[k], m = cs.m0 + mi;
+    if (l < Lb && mi < cs.Mc && (m < 0 ? -m : m) <= l) P[(size_t)cidx * Lb * Lb + l * l + l + m] = acc[k];
+  }
+}
+
+// f_lm += sum_c P[c][l*l + l + m] in chunk order, for l < Lb and m in the m-set.
+static __global__ void unrot_reduce_kernel(const cx<double>* __restrict__ P, int nchunk, int Lb, int m0,
+                                           cx<double>* __restrict__ flm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Lb * Lb) return;
+  int l = (int)sqrt((double)i);
+  if (l * l > i) --l;
+  if ((l + 1) * (l + 1) <= i) ++l;
+  if (i - l * l - l < m0) return;
+  cx<double> s = flm[i];
+  for (int c = 0; c < nchunk; ++c) s = s + P[(size_t)c * Lb * Lb + i];
+  flm[i] = s;
+}
+
+// ---------------------------------------------------------------------------
 // SHT contractions (FP64; O(L^3) total).
 // Forward:  f_lm = sqrt((2l+1)/4pi) sum_{m'>=0} Delta^l_{m'm} Delta^l_{m',-s} G'[m'][mi]
 //           (G' carries (-1)^s i^{m+s} and the folding over +-m').

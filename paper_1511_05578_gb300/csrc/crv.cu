@@ -219,6 +219,7 @@ struct crv_plan_s {
   unsigned flags = 0;
   double lambda = 2;
   bool real = false, mixed = false, wfp32 = false;
+  bool unrot = false;  // coefficients of the unrotated curvelets (CRV_F_UNROTATED)
   std::vector<int> Lj;
   std::vector<double> kappa;  // [J+1][L]
   std::vector<double> phi;    // [L]
@@ -265,9 +266,11 @@ struct crv_plan_s {
   }
   int mc(int Lb) const { return real ? Lb : 2 * Lb - 1; }
   int m0(int Lb) const { return real ? 0 : -(Lb - 1); }
-  int nstep() const { return spin == 0 ? 2 : 1; }
+  // n-set: spin 0 rotated curvelets have zeta_lk = 0 for odd k (vartheta = pi/2); the
+  // unrotated ones sit at n = +-l, which covers every n
+  int nstep() const { return (spin == 0 && !unrot) ? 2 : 1; }
   int n0(int Lb) const {
-    if (spin != 0) return -(Lb - 1);
+    if (nstep() == 1) return -(Lb - 1);
     int n = -(Lb - 1);
     if (n & 1) n += 1;
     return n;
@@ -559,7 +562,13 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
       used_tc = true;
     }
   }
-  if (!used_tc) {
+  if (p->unrot) {
+    dim3 g((cs.Nc + UA_N - 1) / UA_N, ((cs.Mc + 1) / 2 + UA_PAIRS - 1) / UA_PAIRS, Lb);
+    KTimer kt(K_CONTRACT_A, st);
+    unrot_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, X);
+    kt.done();
+    if (!launch_ok("unrot_analysis_kernel")) return false;
+  } else if (!used_tc) {
     dim3 g((cs.Nc + 63) / 64, (cs.Mc + 31) / 32, Lb);
     KTimer kt(K_CONTRACT_A, st);
     contract_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, X);
@@ -628,6 +637,19 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   }
   const int ncols = (int)cs.pitch();
   if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
+  if (p->unrot) {
+    // Xb is consumed by the beta quadrature: its buffer holds the per-chunk sums
+    const int nchunk = (Lb + US_MPC - 1) / US_MPC;
+    cx<double>* P = (cx<double>*)p->wXb;
+    dim3 g((Lb + US_L - 1) / US_L, ((cs.Mc + 1) / 2 + US_PAIRS - 1) / US_PAIRS, nchunk);
+    KTimer kt(K_CONTRACT_S, st);
+    unrot_synthesis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, Y, psi_of<T>(p, j), Lb, cs, P);
+    if (!launch_ok("unrot_synthesis_kernel")) return false;
+    unrot_reduce_kernel<<<(Lb * Lb + 255) / 256, 256, 0, st>>>(P, nchunk, Lb, cs.m0, flm);
+    count_launch();  // the timer counts the first of its two launches
+    kt.done();
+    return launch_ok("unrot_reduce_kernel");
+  }
   if constexpr (sizeof(T) == 4) {
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
     if (p->use_tc)
@@ -803,7 +825,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
   if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");
   if (nrule != CRV_NRULE_CURVELET) return fail(CRV_EINVAL, "unknown nrule");
-  if (flags & ~7u) return fail(CRV_EINVAL, "unknown flag bits");
+  if (flags & ~15u) return fail(CRV_EINVAL, "unknown flag bits");
   if ((flags & CRV_F_REAL) && spin != 0) return fail(CRV_EINVAL, "CRV_F_REAL requires spin 0");
   if (max_batch < 1) return fail(CRV_EINVAL, "max_batch must be >= 1");
   int J = 0;
@@ -821,6 +843,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   auto* p = new crv_plan_s();
   p->L = L; p->lambda = lambda; p->J0 = J0; p->J = J; p->spin = spin; p->flags = flags; p->max_batch = max_batch;
   p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
+  p->unrot = flags & CRV_F_UNROTATED;
   p->Lphi = std::max(1, ceil_pow(lambda, J0));
   p->Lphi = std::min(p->Lphi, L);
   p->Lj.assign(J + 1, 0);
@@ -847,6 +870,12 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
       const double fac = std::sqrt((2.0 * l + 1) / (8 * M_PI * M_PI)) * p->kappa[(size_t)j * L + l];
       if (fac == 0.0) continue;
       if (l == 0) { ps[Lb - 1] = fac / std::sqrt(2.0); continue; }
+      if (p->unrot) {
+        // zeta~_{l,l} = 1/sqrt2, zeta~_{l,-l} = (-1)^l/sqrt2 (Sec. II-B, delta_{l|m|})
+        ps[(size_t)l * N + (l + Lb - 1)] = fac / std::sqrt(2.0);
+        ps[(size_t)l * N + (-l + Lb - 1)] = ((l & 1) ? -fac : fac) / std::sqrt(2.0);
+        continue;
+      }
       // zeta_lk = (d^l_{k,l}(t) + (-1)^l d^l_{k,-l}(t))/sqrt2, d^l_{k,-l} = (-1)^{l-k} d^l_{-k,l}
       edge_row(l, sh, ch, dp);
       for (int kk = -l; kk <= l; ++kk) {
@@ -903,7 +932,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
   {
     const char* e = getenv("CRV_DISABLE_TC");
-    p->use_tc = p->mixed && !(e && e[0] && e[0] != '0');
+    p->use_tc = p->mixed && !p->unrot && !(e && e[0] && e[0] != '0');
   }
   if (stt != CRV_OK) { delete p; return stt; }
   // Delta tables

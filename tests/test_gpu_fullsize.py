@@ -31,6 +31,7 @@ def _built():
 
 
 def _full_case(L, lam, J0, flags, seed, ring_tol, scale_tol, rt_tol, rings_per_scale, spin=0):
+    unrot = bool(flags & crv.CRV_F_UNROTATED)
     real = bool(flags & crv.CRV_F_REAL)
     f = inputs.flm_gaussian(L, seed, spin, real, 3.0 if spin else 2.0)
     fmap = O.sht_inverse(f, L, spin)
@@ -48,7 +49,7 @@ def _full_case(L, lam, J0, flags, seed, ring_tol, scale_tol, rt_tol, rings_per_s
         rings = sorted({0, Lb // 2, Lb - 1} if rings_per_scale >= 3 else {Lb // 3, Lb - 1})
         if Lb <= 64:
             rings = list(range(Lb))
-        ref = O.analysis_rings(flm_o, lam, j, spin, L, rings=rings)
+        ref = O.analysis_rings(flm_o, lam, j, spin, L, rings=rings, unrotated=unrot)
         got = W_from_device(W, j, real)[rings]
         report[j] = rel_l2(got, ref.real if real else ref)
     Wp_ref = O.scaling_map(flm_o, lam, J0, L)
@@ -92,3 +93,12 @@ def test_L1024_mixed_spin2_sampled_rings_and_reconstruction():
     3000), mixed precision: the complex-signal ring and beta kernels at P = 4096 (all m, all n),
     1e-5 relative L2 per sampled ring, per scale and round trip (~175 GB on the device)."""
     _full_case(1024, 2.0, 2, crv.CRV_F_MIXED | crv.CRV_F_W_FP32, 3000, 1e-5, 1e-5, 1e-5, 2, spin=2)
+
+
+def test_L1024_mixed_unrotated_sampled_rings_and_reconstruction():
+    """The benchmark's map shape with the unrotated curvelets (CRV_F_UNROTATED: the paper's
+    single-term l = |n| contraction, every n in the planes), mixed precision (seed 2000):
+    1e-5 relative L2 per sampled ring, per scale (synthesis of scale j alone gives
+    f_lm kappa^(j)(l)^2, Sum_n |zeta~_ln|^2 = 1) and round trip."""
+    _full_case(1024, 2.0, 2, crv.CRV_F_REAL | crv.CRV_F_MIXED | crv.CRV_F_W_FP32 | crv.CRV_F_UNROTATED, 2000,
+               1e-5, 1e-5, 1e-5, 2)

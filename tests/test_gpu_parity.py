@@ -68,10 +68,10 @@ def test_sht_matches_oracle(L, s, real):
     p.close()
 
 
-def _analysis_parity(L, lam, J0, s, real, flags, tol, seed=0, power=2.0):
+def _analysis_parity(L, lam, J0, s, real, flags, tol, seed=0, power=2.0, unrot=False):
     f, fmap = case(L, lam, J0, s, real, seed, power)
-    flm_o, W_o, Wphi_o = O.analysis(fmap, lam, J0, s, L)
-    p = crv.Plan(L, lam, J0, s, flags)
+    flm_o, W_o, Wphi_o = O.analysis(fmap, lam, J0, s, L, unrotated=unrot)
+    p = crv.Plan(L, lam, J0, s, flags | (crv.CRV_F_UNROTATED if unrot else 0))
     W = p.W_tensors(1)
     Wphi = p.Wphi_tensor(1)
     crv.crv_analysis(p.handle, map_to_device(fmap, real), W, Wphi, 1)
@@ -86,7 +86,7 @@ def _analysis_parity(L, lam, J0, s, real, flags, tol, seed=0, power=2.0):
     Wphid = map_to_device(Wphi_o.real if real else Wphi_o, real)
     flm = p.flm_tensor(1)
     crv.crv_synthesis_lm(p.handle, Wd, Wphid, flm, 1)
-    f_ref = O.synthesis_flm(W_o, Wphi_o, lam, J0, s, L)
+    f_ref = O.synthesis_flm(W_o, Wphi_o, lam, J0, s, L, unrotated=unrot)
     errs["synthesis"] = rel_l2(flm[0].cpu().numpy(), f_ref)
     # round trip through the GPU alone
     out = p.map_tensor(1)
@@ -155,3 +155,30 @@ def test_batch_matches_single():
         crv.crv_analysis(p.handle, mb, Wb, None, 4)  # B > max_batch
     crv.crv_analysis(p.handle, mb, Wb, None, 0)  # empty batch is a no-op
     p.close()
+
+
+# ---- unrotated curvelets (CRV_F_UNROTATED): the paper's O(L^3 log L) path --------------
+
+@pytest.mark.parametrize("lam,J0,s,L", [(2.0, 2, 0, 64), (2.0, 1, 2, 32), (1.7, 1, -1, 20)])
+def test_unrotated_plan_kernels_match_oracle(lam, J0, s, L):
+    p = crv.Plan(L, lam, J0, s, crv.CRV_F_UNROTATED)
+    for j in range(J0, p.J + 1):
+        assert np.abs(p.kernel(j) - O.psi(lam, j, s, p.Lj[j], unrotated=True)).max() < 1e-13 + 1e-14 * p.Lj[j], j
+    p.close()
+
+
+@pytest.mark.parametrize("L,lam,J0,s,real", [(64, 2.0, 2, 0, True), (33, 2.0, 2, 0, True), (24, 2.0, 2, 2, False),
+                                             (20, 1.7, 1, -1, False), (9, 3.0, 0, 1, False), (2, 2.0, 1, 0, True)])
+def test_unrotated_fp64(L, lam, J0, s, real):
+    """W~ on the SO(3) grid against the oracle (1e-10 per scale), synthesis of the oracle's W~,
+    and the GPU round trip."""
+    e = _analysis_parity(L, lam, J0, s, real, crv.CRV_F_REAL if real else 0, 1e-10, seed=11, power=3.0 if s else 2.0,
+                         unrot=True)
+    assert e["roundtrip"] < 1e-12
+
+
+@pytest.mark.parametrize("L,lam,J0,s,real", [(64, 2.0, 2, 0, True), (45, 1.7, 1, 0, True), (32, 2.0, 1, 2, False)])
+def test_unrotated_mixed(L, lam, J0, s, real):
+    flags = crv.CRV_F_MIXED | crv.CRV_F_W_FP32 | (crv.CRV_F_REAL if real else 0)
+    e = _analysis_parity(L, lam, J0, s, real, flags, 1e-5, seed=12, power=3.0 if s else 2.0, unrot=True)
+    assert e["roundtrip"] < 1e-5
