@@ -214,13 +214,15 @@ constexpr int UA_PAIRS = 8, UA_N = 64;
 // One (m, n) plane m' = blockIdx.z; a block covers UA_PAIRS column pairs (m, m+1) x UA_N
 // values of n. Phase 1 forms the products with m fastest (coalesced rows Q[m'][l][|m|] and
 // f_lm); phase 2 writes them in column order (per pair row, 2 UA_N contiguous columns).
-// Every column of the plane is written, zeros included (the odd-Mc padding column too).
+// Column pairs (m, m+1) at n that are zero as a whole (|n| < nlo, the first l of the support
+// of kappa^(j), or both |m|, |m+1| > |n|) are not written: the beta transforms skip them.
+// Every other column of the plane is written, zeros included.
 // grid = (ceil(Nc / UA_N), ceil(ceil(Mc/2) / UA_PAIRS), Lb).
 template <class T>
 __global__ void __launch_bounds__(256) unrot_analysis_kernel(const T* __restrict__ Q, int Lmax,
                                                              const cx<double>* __restrict__ flm,
                                                              const T* __restrict__ psi, int Lb, ColSet cs,
-                                                             cx<T>* __restrict__ X) {
+                                                             int nlo, cx<T>* __restrict__ X) {
   __shared__ cx<T> S[UA_N][2 * UA_PAIRS + 1];
   const int N = 2 * Lb - 1, mp = blockIdx.z;
   const int pi0 = blockIdx.y * UA_PAIRS, mi0 = 2 * pi0, ni0 = blockIdx.x * UA_N;
@@ -249,7 +251,9 @@ __global__ void __launch_bounds__(256) unrot_analysis_kernel(const T* __restrict
     const int r = e / (2 * UA_N), w = e % (2 * UA_N), nl = w >> 1, par = w & 1;
     const int ni = ni0 + nl;
     if (pi0 + r >= npairs || ni >= cs.Nc) continue;
-    plane[((size_t)(pi0 + r) * cs.Nc + ni) * 2 + par] = S[nl][2 * r + par];
+    const int n = cs.n0 + ni, an = n < 0 ? -n : n, ma = cs.m0 + 2 * (pi0 + r), mb = ma + 1;
+    const bool live = an >= nlo && ((ma < 0 ? -ma : ma) <= an || (mi0 + 2 * r + 1 < cs.Mc && (mb < 0 ? -mb : mb) <= an));
+    if (live) plane[((size_t)(pi0 + r) * cs.Nc + ni) * 2 + par] = S[nl][2 * r + par];
   }
 }
 
@@ -261,12 +265,14 @@ constexpr int US_L = 32, US_PAIRS = 8, US_MPC = 128;
 // slot k holds n = +l and slot k + 2 the same (l, m) with n = -l. Products are summed in T,
 // flushed to FP64 every 32 m'; the chunk's sums go to P[chunk][l*l + l + m] for every l < Lb,
 // m in the m-set, |m| <= l (zeros included), and unrot_reduce_kernel adds the chunks in order.
+// Columns with l = |n| < nlo (below the support of kappa^(j), Psi~ = 0) are not read: the
+// beta quadrature does not produce them.
 // grid = (ceil(Lb / US_L), ceil(ceil(Mc/2) / US_PAIRS), ceil(Lb / US_MPC)).
 template <class T>
 __global__ void __launch_bounds__(256) unrot_synthesis_kernel(const T* __restrict__ Q, int Lmax,
                                                               const cx<T>* __restrict__ Y,
                                                               const T* __restrict__ psi, int Lb, ColSet cs,
-                                                              cx<double>* __restrict__ P) {
+                                                              int nlo, cx<double>* __restrict__ P) {
   __shared__ T Dm[2][US_L][2 * US_PAIRS + 1];  // Delta^l_{m'm}
   __shared__ T Dn[2][2][US_L];                  // Delta^l_{m',+-l} Psi~_{l,+-l}
   const int N = 2 * Lb - 1;
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(256) unrot_synthesis_kernel(const T* __restric
     ml[k] = 2 * r + (w & 1);
     const int l = l0 + ll[k], mi = mi0 + ml[k], m = cs.m0 + mi;
     const int n = sg ? -l : l;
-    ok[k] = l < Lb && mi < cs.Mc && (m < 0 ? -m : m) <= l && !(sg && l == 0);
+    ok[k] = l < Lb && l >= nlo && mi < cs.Mc && (m < 0 ? -m : m) <= l && !(sg && l == 0);
     col[k] = ok[k] ? ((size_t)(pi0 + r) * cs.Nc + (n - cs.n0)) * 2 + (w & 1) : 0;
   }
   cx<double> acc[4];

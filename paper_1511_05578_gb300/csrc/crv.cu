@@ -220,6 +220,12 @@ struct crv_plan_s {
   double lambda = 2;
   bool real = false, mixed = false, wfp32 = false;
   bool unrot = false;  // coefficients of the unrotated curvelets (CRV_F_UNROTATED)
+  // unrotated plans: per scale, the smallest l >= |s| with kappa^(j)(l) > 0 (columns with
+  // |n| below it are zero, as are those with |m| > |n|) and the column pairs that are not
+  // zero, which are the only ones the beta transforms visit
+  std::vector<int> nlo;
+  std::vector<int*> dpmap;
+  std::vector<int> npmap;
   std::vector<int> Lj;
   std::vector<double> kappa;  // [J+1][L]
   std::vector<double> phi;    // [L]
@@ -433,56 +439,58 @@ static bool run_cols(int kind, const DftTab<T>& tb, int sign, int n, Ld ld, St s
 // contiguous run of pairs (neighbouring columns share sectors through L1; measured).
 template <class T, int NT, int PT>
 static bool run_beta_synth_nt(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* X, cx<T>* Y, ColSet cs,
-                              int kind, cudaStream_t s) {
+                              int kind, PairMap pm, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
   if (!set_smem(beta_synth_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
-  const int npair = num_col_pairs(cs);
+  const int npair = pm.idx ? pm.n : num_col_pairs(cs);
+  if (npair <= 0) return true;
   const int grid = std::max(1, std::min((npair + G - 1) / G, num_sms() * bps));
   KTimer kt(kind, s);
-  beta_synth_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ncols, Lb, X, Y, cs);
+  beta_synth_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ncols, Lb, X, Y, cs, pm);
   kt.done();
   return launch_ok("beta_synth_kernel");
 }
 // Synthesis over beta of all column pairs: X[m'][c] -> Y[b][c].
 template <class T>
 static bool run_beta_synth(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* X, cx<T>* Y, ColSet cs, int kind,
-                           cudaStream_t s) {
+                           cudaStream_t s, PairMap pm = PairMap()) {
   if (ncols <= 0) return true;
   constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_synth_nt<T, NT, 4096>(tb, Lb, ncols, X, Y, cs, kind, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_synth_nt<T, NT, 2048>(tb, Lb, ncols, X, Y, cs, kind, s);
-  return run_beta_synth_nt<T, NT, 0>(tb, Lb, ncols, X, Y, cs, kind, s);
+  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_synth_nt<T, NT, 4096>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_synth_nt<T, NT, 2048>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
+  return run_beta_synth_nt<T, NT, 0>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
 }
 
 template <class T, int NT, int PT>
 static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y,
-                             ColSet cs, T scale, int pa, int pb, int pc, cudaStream_t s) {
+                             ColSet cs, T scale, int pa, int pb, int pc, PairMap pm, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
   if (!set_smem(beta_quad_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
-  const int npair = num_col_pairs(cs);
+  const int npair = pm.idx ? pm.n : num_col_pairs(cs);
+  if (npair <= 0) return true;
   const int grid = std::max(1, std::min((npair + G - 1) / G, num_sms() * bps));
   KTimer kt(K_BETA_QUAD, s);
-  beta_quad_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc);
+  beta_quad_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc, pm);
   kt.done();
   return launch_ok("beta_quad_kernel");
 }
 template <class T>
 static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y, ColSet cs, T scale,
-                          int pa, int pb, int pc, cudaStream_t s) {
+                          int pa, int pb, int pc, cudaStream_t s, PairMap pm = PairMap()) {
   const DftTab<T>& tb = dft_of<T>(fs);
   const CorrTab<T>& ct = corr_of<T>(fs);
   if (ct.Q != tb.P) { g_err = "beta quadrature needs Q == P"; return false; }
   if (ncols <= 0) return true;
   constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
-  return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, s);
+  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
+  return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -565,7 +573,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   if (p->unrot) {
     dim3 g((cs.Nc + UA_N - 1) / UA_N, ((cs.Mc + 1) / 2 + UA_PAIRS - 1) / UA_PAIRS, Lb);
     KTimer kt(K_CONTRACT_A, st);
-    unrot_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, X);
+    unrot_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, p->nlo[j], X);
     kt.done();
     if (!launch_ok("unrot_analysis_kernel")) return false;
   } else if (!used_tc) {
@@ -576,23 +584,28 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
   const int ncols = (int)cs.pitch();
-  if (!run_beta_synth<T>(dft_of<T>(fs), Lb, ncols, X, Xb, cs, K_BETA_SYNTH, st)) return false;
+  const PairMap pm = p->unrot ? PairMap{p->dpmap[j], p->npmap[j]} : PairMap();
+  if (!run_beta_synth<T>(dft_of<T>(fs), Lb, ncols, X, Xb, cs, K_BETA_SYNTH, st, pm)) return false;
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
   const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
+  // unrotated plans: columns |n| < nlo are zero, so the ring steps skip them (nstep = 1 there)
+  const int nlo = p->unrot ? p->nlo[j] : 0, h0 = std::min(nlo, Nh), Nhs = Nh - h0;
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
     if (p->real) {
       // m step on the n >= 0 columns, then the n step with real output, rows in pairs
-      LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, FastDiv((uint32_t)Nh)};
-      StRingMHalf<T> sm{R, N, Nh, FastDiv((uint32_t)Nh)};
-      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nh, lm, sm, st)) return false;
+      if (Nhs > 0) {
+        LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nhs, FastDiv((uint32_t)Nhs), h0, p->unrot};
+        StRingMHalf<T> sm{R, N, Nhs, FastDiv((uint32_t)Nhs), Nh, h0};
+        if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nhs, lm, sm, st)) return false;
+      }
       const int npair = (N + 1) / 2;
-      LdRingNHerm<T> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair)};
+      LdRingNHerm<T> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair), nlo};
       StWRowPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
       if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * npair, ln, sw, st)) return false;
     } else {
-      LdRingN<T> ln{Xb + (size_t)b0 * cs.pitch(), cs, N, FastDiv((uint32_t)cs.Mc)};
+      LdRingN<T> ln{Xb + (size_t)b0 * cs.pitch(), cs, N, FastDiv((uint32_t)cs.Mc), nlo, p->unrot};
       StContig<T> sc{R, N + 1};
       if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
       LdRingM<T> lm{R, cs.Mc, cs.m0, N, N + 1, false, FastDiv((uint32_t)N)};
@@ -614,6 +627,8 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   const int Rr = ring_chunk(p, Lb, sizeof(cx<T>));
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
   const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
+  // unrotated plans: only the columns |n| >= nlo are needed downstream
+  const int nlo = p->unrot ? p->nlo[j] : 0, h0 = std::min(nlo, Nh), Nhs = Nh - h0;
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
     if (p->real) {
@@ -621,11 +636,13 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
       // which also fills the n < 0 columns by conjugation
       const int nrows = nr * N;
       LdWRowPair<T, InT> lw{W + (size_t)b0 * wstride, N, nrows};
-      StRingNPairHalf<T> sn{R, Nh, cs.nstep, N, nrows, (T)1 / (T)N};
+      StRingNPairHalf<T> sn{R, Nh, cs.nstep, N, nrows, (T)1 / (T)N, h0};
       if (!run_rows<T>(K_RING_FWD_G, dft_of<T>(fs), -1, (nrows + 1) / 2, lw, sn, st)) return false;
-      LdRingAHalf<T> la{R, N, Nh, FastDiv((uint32_t)Nh)};
-      StRingAHalf<T> sa{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, (T)1 / (T)N, FastDiv((uint32_t)Nh)};
-      if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * Nh, la, sa, st)) return false;
+      if (Nhs > 0) {
+        LdRingAHalf<T> la{R, N, Nhs, FastDiv((uint32_t)Nhs), Nh, h0};
+        StRingAHalf<T> sa{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nhs, (T)1 / (T)N, FastDiv((uint32_t)Nhs), h0};
+        if (!run_cols<T>(K_RING_FWD_A, dft_of<T>(fs), -1, nr * Nhs, la, sa, st)) return false;
+      }
     } else {
       LdWRow<T, InT> lw{W + (size_t)b0 * wstride, N, false};
       StRingN<T> sn{R, cs.Nc, cs.n0, cs.nstep, N, (T)1 / (T)N};
@@ -636,14 +653,15 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
     }
   }
   const int ncols = (int)cs.pitch();
-  if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st)) return false;
+  const PairMap pm = p->unrot ? PairMap{p->dpmap[j], p->npmap[j]} : PairMap();
+  if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st, pm)) return false;
   if (p->unrot) {
     // Xb is consumed by the beta quadrature: its buffer holds the per-chunk sums
     const int nchunk = (Lb + US_MPC - 1) / US_MPC;
     cx<double>* P = (cx<double>*)p->wXb;
     dim3 g((Lb + US_L - 1) / US_L, ((cs.Mc + 1) / 2 + US_PAIRS - 1) / US_PAIRS, nchunk);
     KTimer kt(K_CONTRACT_S, st);
-    unrot_synthesis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, Y, psi_of<T>(p, j), Lb, cs, P);
+    unrot_synthesis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, Y, psi_of<T>(p, j), Lb, cs, nlo, P);
     if (!launch_ok("unrot_synthesis_kernel")) return false;
     unrot_reduce_kernel<<<(Lb * Lb + 255) / 256, 256, 0, st>>>(P, nchunk, Lb, cs.m0, flm);
     count_launch();  // the timer counts the first of its two launches
@@ -886,7 +904,32 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
       }
     }
   }
+  p->nlo.assign(J + 1, 0);
+  for (int j = J0; j <= J; ++j) {
+    int l = std::abs(spin);
+    while (l < p->Lj[j] && !(p->kappa[(size_t)j * L + l] > 0)) ++l;
+    p->nlo[j] = l;
+  }
   int stt = CRV_OK;
+  if (p->unrot) {
+    // column pairs (m, m+1) at n with a nonzero column: |n| >= nlo and min(|m|, |m+1|) <= |n|
+    p->dpmap.assign(J + 1, nullptr);
+    p->npmap.assign(J + 1, 0);
+    for (int j = J0; j <= J && stt == CRV_OK; ++j) {
+      const ColSet cs = p->colset(p->Lj[j]);
+      std::vector<int> idx;
+      for (int i = 0; i < (cs.Mc + 1) / 2; ++i)
+        for (int ni = 0; ni < cs.Nc; ++ni) {
+          const int m = cs.m0 + 2 * i, an = std::abs(cs.n0 + ni);
+          const bool b_ok = 2 * i + 1 < cs.Mc && std::abs(m + 1) <= an;
+          if (an >= p->nlo[j] && (std::abs(m) <= an || b_ok)) idx.push_back(i * cs.Nc + ni);
+        }
+      p->npmap[j] = (int)idx.size();
+      p->dpmap[j] = p->dalloc<int>(idx.size(), &stt);
+      if (stt == CRV_OK && !idx.empty())
+        cudaMemcpy(p->dpmap[j], idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+  }
   // device tables
   const size_t n3 = (size_t)L * L * L;
   p->dQ = p->dalloc<double>(n3, &stt);

@@ -155,12 +155,20 @@ __device__ __forceinline__ ColPair col_pair(const ColSet& cs, int p) {
   return r;
 }
 __host__ __device__ inline int num_col_pairs(const ColSet& cs) { return (cs.Mc + 1) / 2 * cs.Nc; }
+// Optional list of the column pairs a beta transform visits (the others are known to be
+// zero and are neither read nor written): pair idx[q], q < n; idx = nullptr visits all.
+struct PairMap {
+  const int* idx = nullptr;
+  int n = 0;
+};
 
 
 // Ring inverse, step over n: sequence (b, mi) of the planes Xb[b] -> T[b][mi][g].
 template <class T>
 struct LdRingN {
   const cx<T>* Xb; ColSet cs; int N; FastDiv fMc;
+  int nlo = 0;         // columns |n| < nlo are zero (and not read)
+  bool mzero = false;  // columns |m| > |n| are zero (unrotated curvelets)
   __device__ cx<T> operator()(int c, int j) const {
     const int b = (int)fMc.div((uint32_t)c), mi = c - b * cs.Mc;
     // j = n mod N; find ni with n0 + nstep*ni == n
@@ -169,6 +177,8 @@ struct LdRingN {
     if (d < 0 || (d & (cs.nstep - 1))) return mk<T>(0, 0);
     const int ni = d >> (cs.nstep - 1);
     if (ni >= cs.Nc) return mk<T>(0, 0);
+    const int an = n < 0 ? -n : n, m = cs.m0 + mi;
+    if (an < nlo || (mzero && (m < 0 ? -m : m) > an)) return mk<T>(0, 0);
     return Xb[(size_t)b * cs.pitch() + cs.col(mi, ni)];
   }
 };
@@ -291,26 +301,37 @@ template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 
 // m < 0 by the conjugate of the -n column -> R[b][a][h].
 template <class T>
 struct LdRingMHalf {
-  const cx<T>* Xb; ColSet cs; int ni0, N, Nh; FastDiv fNh;
-  __device__ const cx<T>* at(int c, int j, int& m) const {
-    const int b = (int)fNh.div((uint32_t)c), ni = ni0 + (c - b * Nh);
+  const cx<T>* Xb; ColSet cs; int ni0, N, Nh; FastDiv fNh;  // Nh columns per ring, from h0 on
+  int h0 = 0;          // first column transformed
+  bool mzero = false;  // entries |m| > n are zero and not read (unrotated curvelets)
+  __device__ const cx<T>* at(int c, int j, int& m, bool& z) const {
+    const int b = (int)fNh.div((uint32_t)c), h = h0 + (c - b * Nh), ni = ni0 + h;
     m = (j <= (N - 1) / 2) ? j : j - N;
+    z = mzero && (m < 0 ? -m : m) > h * cs.nstep;
     const cx<T>* base = Xb + (size_t)b * cs.pitch();
     return m >= 0 ? base + cs.col(m, ni) : base + cs.col(-m, cs.Nc - 1 - ni);
   }
   __device__ cx<T> operator()(int c, int j) const {
     int m;
-    const cx<T> v = *at(c, j, m);
+    bool z;
+    const cx<T>* q = at(c, j, m, z);
+    if (z) return mk<T>(0, 0);
+    const cx<T> v = *q;
     return m >= 0 ? v : conj(v);
   }
-  __device__ void pf(int c, int j) const { int m; pf_l1(at(c, j, m)); }
+  __device__ void pf(int c, int j) const {
+    int m;
+    bool z;
+    const cx<T>* q = at(c, j, m, z);
+    if (!z) pf_l1(q);
+  }
 };
 template <class T>
-struct StRingMHalf {
-  cx<T>* R; int N, Nh; FastDiv fNh;
+struct StRingMHalf {  // R[b][a][h0 + h], rows of Rp columns; Nh columns per ring
+  cx<T>* R; int N, Nh; FastDiv fNh; int Rp, h0;
   __device__ void operator()(int c, int k, cx<T> v, cx<T>) const {
     const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh;
-    R[((size_t)b * N + k) * Nh + h] = v;
+    R[((size_t)b * N + k) * Rp + h0 + h] = v;
   }
 };
 // Analysis, step over n (sign +1) with real output: rows a1 = 2 ap and a2 = 2 ap + 1 of
@@ -319,11 +340,12 @@ struct StRingMHalf {
 template <class T>
 struct LdRingNHerm {
   const cx<T>* R; int N, Nh, nstep, npair; FastDiv fP;
+  int nlo = 0;  // |n| < nlo: zero (those columns of R are not written)
   __device__ cx<T> operator()(int c, int j) const {
     const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair), a2 = a1 + 1;
     const int n = (j <= (N - 1) / 2) ? j : j - N;
     const int an = n < 0 ? -n : n;
-    if (an & (nstep - 1)) return mk<T>(0, 0);
+    if ((an & (nstep - 1)) || an < nlo) return mk<T>(0, 0);
     const int h = an >> (nstep - 1);
     const cx<T>* rb = R + (size_t)b * N * Nh;
     cx<T> x = rb[(size_t)a1 * Nh + h];
@@ -335,7 +357,7 @@ struct LdRingNHerm {
     const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair);
     const int n = (j <= (N - 1) / 2) ? j : j - N;
     const int an = n < 0 ? -n : n;
-    if (an & (nstep - 1)) return;
+    if ((an & (nstep - 1)) || an < nlo) return;
     const cx<T>* q = R + (size_t)b * N * Nh + (size_t)a1 * Nh + (an >> (nstep - 1));
     pf_l1(q);
     if (a1 + 1 < N) pf_l1(q + Nh);
@@ -355,10 +377,11 @@ struct StWRowPair {  // W[b][a][g], real: row a1 <- Re, a2 <- Im
 template <class T>
 struct StRingNPairHalf {
   cx<T>* U; int Nh, nstep, N, nrows; T scale;
+  int h0 = 0;  // columns h < h0 are not needed
   __device__ void operator()(int c, int k, cx<T> z, cx<T> zn) const {
     if (k > (N - 1) / 2 || (k & (nstep - 1))) return;  // n = k >= 0 in the n-set
     const int h = k >> (nstep - 1);
-    if (h >= Nh) return;
+    if (h >= Nh || h < h0) return;
     const T hs = scale * (T)0.5;
     U[(size_t)(2 * c) * Nh + h] = mk<T>((z.re + zn.re) * hs, (z.im - zn.im) * hs);
     if (2 * c + 1 < nrows) U[(size_t)(2 * c + 1) * Nh + h] = mk<T>((z.im + zn.im) * hs, (zn.re - z.re) * hs);
@@ -368,21 +391,22 @@ template <class T> struct Mirror<StRingNPairHalf<T>> { static constexpr int valu
 // Synthesis, step over a (sign -1) for n >= 0: column (b, h) of U[b][a][h] -> D_m; the
 // m >= 0 outputs go to column ni of Xb, and conj(D_{-m}) to the mirror column (-n).
 template <class T>
-struct LdRingAHalf {
-  const cx<T>* U; int N, Nh; FastDiv fNh;
+struct LdRingAHalf {  // U[b][a][h0 + h], rows of Up columns; Nh columns per ring
+  const cx<T>* U; int N, Nh; FastDiv fNh; int Up, h0;
   __device__ const cx<T>* at(int c, int j) const {
-    const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh;
-    return U + ((size_t)b * N + j) * Nh + h;
+    const int b = (int)fNh.div((uint32_t)c), h = h0 + (c - b * Nh);
+    return U + ((size_t)b * N + j) * Up + h;
   }
   __device__ cx<T> operator()(int c, int j) const { return *at(c, j); }
   __device__ void pf(int c, int j) const { pf_l1(at(c, j)); }
 };
 template <class T>
 struct StRingAHalf {
-  cx<T>* Xb; ColSet cs; int ni0, N, Nh; T scale; FastDiv fNh;
+  cx<T>* Xb; ColSet cs; int ni0, N, Nh; T scale; FastDiv fNh;  // Nh columns per ring, from h0 on
+  int h0 = 0;
   __device__ void operator()(int c, int k, cx<T> v, cx<T> vn) const {
     if (k >= cs.Mc) return;  // m = k >= 0 (Mc = Lb <= (N + 1) / 2)
-    const int b = (int)fNh.div((uint32_t)c), h = c - b * Nh, ni = ni0 + h;
+    const int b = (int)fNh.div((uint32_t)c), h = h0 + (c - b * Nh), ni = ni0 + h;
     cx<T>* plane = Xb + (size_t)b * cs.pitch();
     plane[cs.col(k, ni)] = v * scale;
     if (h > 0) plane[cs.col(k, cs.Nc - 1 - ni)] = conj(vn) * scale;
@@ -484,10 +508,10 @@ __device__ __forceinline__ void load_pair_ext(cx<T> (&v)[16], const cx<T>* __res
 template <class T, int NT, int PT>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_kernel(DftTab<T> tb, int ncols, int Lb,
                                                                      const cx<T>* __restrict__ X,
-                                                                     cx<T>* __restrict__ Y, ColSet cs) {
+                                                                     cx<T>* __restrict__ Y, ColSet cs, PairMap pm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
-  const int npair = num_col_pairs(cs);
+  const int npair = pm.idx ? pm.n : num_col_pairs(cs);
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
@@ -496,7 +520,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_k
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
     const int p = s0 + g;
     const bool valid = p < s_end;
-    const ColPair cp = valid ? col_pair(cs, p) : ColPair{0, -1, 0};
+    const ColPair cp = valid ? col_pair(cs, pm.idx ? pm.idx[p] : p) : ColPair{0, -1, 0};
     cx<T> v[16];
     load_pair_ext<T>(v, X, ncols, cp, valid, Lb, N, t, TP, 0, buf);
 #pragma unroll
@@ -552,10 +576,10 @@ template <class T, int NT, int PT>
 __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_kernel(DftTab<T> tb, CorrTab<T> ct, int ncols, int Lb,
                                                                     const cx<T>* __restrict__ Xb,
                                                                     cx<T>* __restrict__ Y, ColSet cs, T scale, int pa,
-                                                                    int pb, int pc) {
+                                                                    int pb, int pc, PairMap pm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = tb.N, Q = PT ? PT : ct.Q, TP = (PT ? PT : tb.P) >> 4, G = NT / TP;
-  const int npair = num_col_pairs(cs);
+  const int npair = pm.idx ? pm.n : num_col_pairs(cs);
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
@@ -565,7 +589,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
     const int p = s0 + g;
     const bool valid = p < s_end;
-    const ColPair cp = valid ? col_pair(cs, p) : ColPair{0, -1, 0};
+    const ColPair cp = valid ? col_pair(cs, pm.idx ? pm.idx[p] : p) : ColPair{0, -1, 0};
     // extensions to the 2Lb-1 nodes of the full circle, summed, then the chirp
     cx<T> v[16];
     load_pair_ext<T>(v, Xb, ncols, cp, valid, Lb, N, t, TP, 1, buf);
