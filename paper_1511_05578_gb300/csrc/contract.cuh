@@ -210,71 +210,87 @@ __global__ void __launch_bounds__(256) contract_synthesis_kernel(const T* __rest
 // every n (nstep = 1), pair-interleaved as everywhere.
 // ---------------------------------------------------------------------------
 constexpr int UA_PAIRS = 8, UA_N = 64;
+// m' planes per block of the analysis fill and per step of the synthesis loop
+template <class T> struct UnrotPlanes { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
-// One (m, n) plane m' = blockIdx.z; a block covers UA_PAIRS column pairs (m, m+1) x UA_N
-// values of n. Phase 1 forms the products with m fastest (coalesced rows Q[m'][l][|m|] and
-// f_lm); phase 2 writes them in column order (per pair row, 2 UA_N contiguous columns).
+// A block covers UnrotPlanes (m, n) planes m' from blockIdx.z * UnrotPlanes on, and
+// UA_PAIRS column pairs (m, m+1) x UA_N values of n. Phase 1 forms the products with m
+// fastest (coalesced rows Q[m'][l][|m|] and f_lm, the latter once for all planes); phase 2
+// writes them in column order (per pair row, 2 UA_N contiguous columns).
 // Column pairs (m, m+1) at n that are zero as a whole (|n| < nlo, the first l of the support
 // of kappa^(j), or both |m|, |m+1| > |n|) are not written: the beta transforms skip them.
 // Every other column of the plane is written, zeros included.
-// grid = (ceil(Nc / UA_N), ceil(ceil(Mc/2) / UA_PAIRS), Lb).
+// grid = (ceil(Nc / UA_N), ceil(ceil(Mc/2) / UA_PAIRS), ceil(Lb / UnrotPlanes)).
 template <class T>
 __global__ void __launch_bounds__(256) unrot_analysis_kernel(const T* __restrict__ Q, int Lmax,
                                                              const cx<double>* __restrict__ flm,
                                                              const T* __restrict__ psi, int Lb, ColSet cs,
                                                              int nlo, cx<T>* __restrict__ X) {
-  __shared__ cx<T> S[UA_N][2 * UA_PAIRS + 1];
-  const int N = 2 * Lb - 1, mp = blockIdx.z;
+  constexpr int MPB = UnrotPlanes<T>::value, E = UA_N * 2 * UA_PAIRS / 256;
+  __shared__ cx<T> S[MPB][UA_N][2 * UA_PAIRS + 1];
+  const int N = 2 * Lb - 1, mpb = blockIdx.z * MPB;
   const int pi0 = blockIdx.y * UA_PAIRS, mi0 = 2 * pi0, ni0 = blockIdx.x * UA_N;
-  for (int e = threadIdx.x; e < UA_N * 2 * UA_PAIRS; e += blockDim.x) {
-    const int nl = e / (2 * UA_PAIRS), ml = e % (2 * UA_PAIRS);
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int e = t + 256 * k, nl = e / (2 * UA_PAIRS), ml = e % (2 * UA_PAIRS);
     const int mi = mi0 + ml, ni = ni0 + nl;
-    cx<T> v = mk<T>(0, 0);
-    if (mi < cs.Mc && ni < cs.Nc) {
-      const int m = cs.m0 + mi, n = cs.n0 + ni;
-      const int l = n < 0 ? -n : n, am = m < 0 ? -m : m;
-      if (l >= am && l >= mp) {
-        const T ps = psi[(size_t)l * N + (n + Lb - 1)];
-        if (ps != (T)0) {
-          const T d = delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, n) * ps;
-          const cx<double> f = flm[l * l + l + m];
-          v = mul_ipow(mk<T>(d * (T)f.re, d * (T)f.im), imod(n - m, 4));
-        }
-      }
+    const int m = cs.m0 + mi, n = cs.n0 + ni;
+    const int l = n < 0 ? -n : n, am = m < 0 ? -m : m;
+    cx<T> base = mk<T>(0, 0);
+    T ps = 0;
+    const bool live = mi < cs.Mc && ni < cs.Nc && l >= am && l >= mpb;
+    if (live) ps = psi[(size_t)l * N + (n + Lb - 1)];
+    if (ps != (T)0) {
+      const cx<double> f = flm[l * l + l + m];
+      base = mul_ipow(mk<T>(ps * (T)f.re, ps * (T)f.im), imod(n - m, 4));
     }
-    S[nl][ml] = v;
+    T d[MPB];
+#pragma unroll
+    for (int q = 0; q < MPB; ++q) {
+      const int mp = mpb + q;
+      d[q] = (ps != (T)0 && mp < Lb && l >= mp) ? delta_q(Q, Lmax, mp, l, m) * delta_q(Q, Lmax, mp, l, n) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < MPB; ++q) S[q][nl][ml] = base * d[q];
   }
   __syncthreads();
   const int npairs = (cs.Mc + 1) >> 1;
-  cx<T>* plane = X + (size_t)mp * cs.pitch();
-  for (int e = threadIdx.x; e < UA_PAIRS * 2 * UA_N; e += blockDim.x) {
-    const int r = e / (2 * UA_N), w = e % (2 * UA_N), nl = w >> 1, par = w & 1;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int e = t + 256 * k, r = e / (2 * UA_N), w = e % (2 * UA_N), nl = w >> 1, par = w & 1;
     const int ni = ni0 + nl;
     if (pi0 + r >= npairs || ni >= cs.Nc) continue;
     const int n = cs.n0 + ni, an = n < 0 ? -n : n, ma = cs.m0 + 2 * (pi0 + r), mb = ma + 1;
     const bool live = an >= nlo && ((ma < 0 ? -ma : ma) <= an || (mi0 + 2 * r + 1 < cs.Mc && (mb < 0 ? -mb : mb) <= an));
-    if (live) plane[((size_t)(pi0 + r) * cs.Nc + ni) * 2 + par] = S[nl][2 * r + par];
+    if (!live) continue;
+    const size_t c = ((size_t)(pi0 + r) * cs.Nc + ni) * 2 + par;
+#pragma unroll
+    for (int q = 0; q < MPB; ++q)
+      if (mpb + q < Lb) X[(size_t)(mpb + q) * cs.pitch() + c] = S[q][nl][2 * r + par];
   }
 }
 
 constexpr int US_L = 32, US_PAIRS = 8, US_MPC = 128;
 
 // Synthesis: a block covers US_L values of l (both n = +l and n = -l) x US_PAIRS column
-// pairs and a chunk of US_MPC values of m'. Per m' the rows Delta^l_{m'm} of the tile pass
-// through shared memory (loaded m fastest), the Y' columns are read in column order; thread
-// slot k holds n = +l and slot k + 2 the same (l, m) with n = -l. Products are summed in T,
-// flushed to FP64 every 32 m'; the chunk's sums go to P[chunk][l*l + l + m] for every l < Lb,
-// m in the m-set, |m| <= l (zeros included), and unrot_reduce_kernel adds the chunks in order.
-// Columns with l = |n| < nlo (below the support of kappa^(j), Psi~ = 0) are not read: the
-// beta quadrature does not produce them.
+// pairs and a chunk of US_MPC values of m', UnrotPlanes at a time: the rows Delta^l_{m'm} of
+// the tile pass through shared memory (loaded m fastest), the Y' columns are read in column
+// order; thread slot k holds n = +l and slot k + 2 the same (l, m) with n = -l. Products are
+// summed in T, flushed to FP64 every 32 m'; the chunk's sums go to P[chunk][l*l + l + m] for
+// every l < Lb, m in the m-set, |m| <= l (zeros included), and unrot_reduce_kernel adds the
+// chunks in order. Columns with l = |n| < nlo (below the support of kappa^(j), Psi~ = 0) are
+// not read: the beta quadrature does not produce them.
 // grid = (ceil(Lb / US_L), ceil(ceil(Mc/2) / US_PAIRS), ceil(Lb / US_MPC)).
 template <class T>
 __global__ void __launch_bounds__(256) unrot_synthesis_kernel(const T* __restrict__ Q, int Lmax,
                                                               const cx<T>* __restrict__ Y,
                                                               const T* __restrict__ psi, int Lb, ColSet cs,
                                                               int nlo, cx<double>* __restrict__ P) {
-  __shared__ T Dm[2][US_L][2 * US_PAIRS + 1];  // Delta^l_{m'm}
-  __shared__ T Dn[2][2][US_L];                  // Delta^l_{m',+-l} Psi~_{l,+-l}
+  constexpr int MPS = UnrotPlanes<T>::value;
+  static_assert(US_MPC % MPS == 0 && 32 % MPS == 0, "plane step divides the chunk and the flush period");
+  __shared__ T Dm[2][MPS][US_L][2 * US_PAIRS + 1];  // Delta^l_{m'm}
+  __shared__ T Dn[2][MPS][2][US_L];                  // Delta^l_{m',+-l} Psi~_{l,+-l}
   const int N = 2 * Lb - 1;
   const int l0 = blockIdx.x * US_L, pi0 = blockIdx.y * US_PAIRS, mi0 = 2 * pi0;
   const int mp0 = blockIdx.z * US_MPC;
@@ -300,32 +316,38 @@ __global__ void __launch_bounds__(256) unrot_synthesis_kernel(const T* __restric
   cx<T> part[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) { acc[k] = mk(0.0, 0.0); part[k] = mk<T>(0, 0); }
-  for (int mp = mp0; mp < mp1; ++mp) {
-    const int bf = mp & 1;
-    for (int e = t; e < US_L * 2 * US_PAIRS; e += 256) {
-      const int a = e / (2 * US_PAIRS), b = e % (2 * US_PAIRS);
-      const int l = l0 + a, mi = mi0 + b, m = cs.m0 + mi;
+  int it = 0;
+  for (int mpb = mp0; mpb < mp1; mpb += MPS, ++it) {
+    const int bf = it & 1;
+    for (int e = t; e < MPS * US_L * 2 * US_PAIRS; e += 256) {
+      const int q = e / (US_L * 2 * US_PAIRS), a = (e / (2 * US_PAIRS)) % US_L, b = e % (2 * US_PAIRS);
+      const int mp = mpb + q, l = l0 + a, mi = mi0 + b, m = cs.m0 + mi;
       T d = 0;
-      if (l < Lb && l >= mp && mi < cs.Mc && (m < 0 ? -m : m) <= l) d = delta_q(Q, Lmax, mp, l, m);
-      Dm[bf][a][b] = d;
+      if (mp < mp1 && l < Lb && l >= mp && mi < cs.Mc && (m < 0 ? -m : m) <= l) d = delta_q(Q, Lmax, mp, l, m);
+      Dm[bf][q][a][b] = d;
     }
-    if (t < 2 * US_L) {
-      const int sg = t / US_L, a = t % US_L, l = l0 + a, n = sg ? -l : l;
+    if (t < MPS * 2 * US_L) {
+      const int q = t / (2 * US_L), sg = (t / US_L) & 1, a = t % US_L, mp = mpb + q, l = l0 + a, n = sg ? -l : l;
       T d = 0;
-      if (l < Lb && l >= mp) d = delta_q(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)];
-      Dn[bf][sg][a] = d;
+      if (mp < mp1 && l < Lb && l >= mp) d = delta_q(Q, Lmax, mp, l, n) * psi[(size_t)l * N + (n + Lb - 1)];
+      Dn[bf][q][sg][a] = d;
     }
     __syncthreads();
-    const cx<T>* Yp = Y + (size_t)mp * pitch;
+    cx<T> y[MPS][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (!ok[k]) continue;
-      const cx<T> y = Yp[col[k]];
-      const T c = Dm[bf][ll[k]][ml[k]] * Dn[bf][k >> 1][ll[k]];
-      part[k].re += c * y.re;
-      part[k].im += c * y.im;
-    }
-    if (((mp - mp0) & 31) == 31) {
+    for (int q = 0; q < MPS; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        y[q][k] = (ok[k] && mpb + q < mp1) ? Y[(size_t)(mpb + q) * pitch + col[k]] : mk<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < MPS; ++q)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const T c = Dm[bf][q][ll[k]][ml[k]] * Dn[bf][q][k >> 1][ll[k]];
+        part[k].re += c * y[q][k].re;
+        part[k].im += c * y[q][k].im;
+      }
+    if (((mpb + MPS - mp0) & 31) == 0) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         acc[k].re += (double)part[k].re; acc[k].im += (double)part[k].im;

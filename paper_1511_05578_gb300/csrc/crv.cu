@@ -571,7 +571,8 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     }
   }
   if (p->unrot) {
-    dim3 g((cs.Nc + UA_N - 1) / UA_N, ((cs.Mc + 1) / 2 + UA_PAIRS - 1) / UA_PAIRS, Lb);
+    constexpr int MPB = UnrotPlanes<T>::value;
+    dim3 g((cs.Nc + UA_N - 1) / UA_N, ((cs.Mc + 1) / 2 + UA_PAIRS - 1) / UA_PAIRS, (Lb + MPB - 1) / MPB);
     KTimer kt(K_CONTRACT_A, st);
     unrot_analysis_kernel<T><<<g, 256, 0, st>>>(q_of<T>(p), p->L, flm, psi_of<T>(p, j), Lb, cs, p->nlo[j], X);
     kt.done();
