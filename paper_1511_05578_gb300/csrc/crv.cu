@@ -247,7 +247,8 @@ struct crv_plan_s {
   void* wR = nullptr;
   bool use_tc = false;   // tensor-core contractions (mixed plans)
   std::vector<TcTab> tabA, tabS;  // per scale: B operand tables of the two contractions
-  int* d_err = nullptr;   // set by kernels whose bounded waits gave up
+  std::vector<TcATab> tabAA;        // per scale: chunk offsets of the per-map A tables (one buffer)
+  int* d_err = nullptr;   // [0]: set by kernels whose bounded waits gave up; [1]: tile counter of the tensor-core engine
   size_t vol_bytes = 0, ring_bytes = 0;
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -566,7 +567,9 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   bool used_tc = false;
   if constexpr (sizeof(T) == 4) {
     if (p->use_tc) {
-      if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->tabA[j], Lb, cs, (cx<float>*)X, p->d_err, st)) return false;
+      if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->tabA[j], Lb, cs, (cx<float>*)X, p->d_err, p->d_err + 1, st,
+                       p->tabAA[j]))
+        return false;
       used_tc = true;
     }
   }
@@ -673,6 +676,7 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
     if (p->use_tc)
       return tc_synthesis(p->dQ32, p->L, (const cx<float>*)Y, p->tabS[j], Lb, cs, (cx<float>*)p->wXb, flm, p->d_err,
+                          p->d_err + 1,
                           st);
   }
   const int mchunk = 16;
@@ -830,6 +834,38 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
       (dir == 0 ? p->tabA : p->tabS)[j] = t;
     }
   }
+  // per-map A tables of the analysis: offsets per scale, one buffer for the largest scale
+  p->tabAA.assign(p->J + 1, TcATab());
+  long long amax = 0;
+  for (int j = p->J0; j <= p->J; ++j) {
+    const ColSet cs = p->colset(p->Lj[j]);
+    std::vector<int2> range;
+    int nmt = 0;
+    tc_analysis_a_ranges(p->Lj[j], cs, range, nmt);
+    std::vector<long long> base(range.size());
+    long long total = 0;
+    for (size_t i = 0; i < range.size(); ++i) {
+      base[i] = total - range[i].x;
+      total += range[i].y;
+    }
+    amax = std::max(amax, total);
+    long long* dbase = p->dalloc<long long>(base.size(), &stt);
+    int2* drange = p->dalloc<int2>(range.size(), &stt);
+    if (stt != CRV_OK) return stt;
+    cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    p->tabAA[j].base = dbase;
+    p->tabAA[j].range = drange;
+    p->tabAA[j].nmt = nmt;
+  }
+  const size_t na = (size_t)std::max<long long>(amax, 1) * TC_ACHUNK_FLOATS;
+  float* ahi = p->dalloc<float>(na, &stt);
+  float* alo = p->dalloc<float>(na, &stt);
+  if (stt != CRV_OK) return stt;
+  for (int j = p->J0; j <= p->J; ++j) {
+    p->tabAA[j].hi = ahi;
+    p->tabAA[j].lo = alo;
+  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CRV_ECUDA, "contraction table build failed");
   return CRV_OK;
 }
@@ -965,8 +1001,8 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->wX = p->dalloc<unsigned char>(p->vol_bytes, &stt);
   // Xb; in the mixed path it also holds the synthesis products Z[m'][mi][l] (L x Mc x L)
   p->wXb = p->dalloc<unsigned char>(std::max(p->vol_bytes, (size_t)L * Mc * L * el), &stt);
-  p->d_err = p->dalloc<int>(1, &stt);
-  if (stt == CRV_OK) cudaMemset(p->d_err, 0, sizeof(int));
+  p->d_err = p->dalloc<int>(2, &stt);
+  if (stt == CRV_OK) cudaMemset(p->d_err, 0, 2 * sizeof(int));
   {
     // ring-chunk buffer: at least one ring, at most all rings, 256 MB (larger chunks: fewer
     // launches; measured 48 -> 120 MB monotonically faster)

@@ -38,11 +38,11 @@ struct AnalysisProb {
   static constexpr bool kBulkB = true;
   const float* Q; int Lmax; const cx<float>* flm; TcTab tb; int Lb; ColSet cs; cx<float>* X;
   // K chunks: the table's run for (m', n-tile), skipping chunks below min |m| of the m-tile
-  __device__ void tile(int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
-    mp = blockIdx.z; mi0 = blockIdx.y * (BM / 2); n0i = blockIdx.x * BNC;
+  __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
+    mp = bz; mi0 = by * (BM / 2); n0i = bx * BNC;
     const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
     const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
-    const int2 rg = tb.range[mp * tb.ntiles + blockIdx.x];
+    const int2 rg = tb.range[mp * tb.ntiles + bx];
     const int c0 = max(rg.x, amin / TC_CHUNK_K), c1 = rg.x + rg.y;
     kb = c0 * TC_CHUNK_K;
     ke = max(c0, c1) * TC_CHUNK_K;
@@ -94,13 +94,25 @@ struct AnalysisProb {
   }
 };
 
+// Analysis with the A operand from the per-map tables (persistent engine).
+struct AnalysisProbA : AnalysisProb {
+  static constexpr bool kBulkA = true;
+  TcATab ta;
+  __device__ void a_tiles(int mp, int mi0, int k0, const void*& hi, const void*& lo) const {
+    const size_t off =
+        (size_t)(ta.base[mp * ta.nmt + mi0 / (BM / 2)] + k0 / TC_CHUNK_K) * TC_ACHUNK_FLOATS;
+    hi = ta.hi + off;
+    lo = ta.lo + off;
+  }
+};
+
 struct SynthesisProb {
   static constexpr bool kBulkB = true;
   const cx<float>* Y; TcTab tb; int Lb; ColSet cs; cx<float>* Z;
   // K chunks over ni: the table's run for (m', l-tile) (empty if m' > max l of the tile)
-  __device__ void tile(int& mp, int& mi0, int& l0, int& kb, int& ke) const {
-    mp = blockIdx.z; mi0 = blockIdx.y * (BM / 2); l0 = blockIdx.x * BNC;
-    const int2 rg = tb.range[mp * tb.ntiles + blockIdx.x];
+  __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& l0, int& kb, int& ke) const {
+    mp = bz; mi0 = by * (BM / 2); l0 = bx * BNC;
+    const int2 rg = tb.range[mp * tb.ntiles + bx];
     kb = rg.x * TC_CHUNK_K;
     ke = (rg.x + rg.y) * TC_CHUNK_K;
   }
@@ -238,6 +250,35 @@ __global__ void __launch_bounds__(256) fill_synthesis_table_kernel(const float* 
   }
 }
 
+// Per-map A tables of the analysis: block (m-tile, m'), thread = row r = 2 (m - mi0) + Re|Im.
+__global__ void __launch_bounds__(TC_A_ROWS) fill_analysis_a_kernel(const float* __restrict__ Q, int Lmax,
+                                                                     const cx<float>* __restrict__ flm, int Lb,
+                                                                     ColSet cs, TcATab t) {
+  const int mp = blockIdx.y, mt = blockIdx.x, r = threadIdx.x;
+  const int2 rg = t.range[mp * t.nmt + mt];
+  const long long base = t.base[mp * t.nmt + mt];
+  const int mi = mt * (TC_A_ROWS / 2) + (r >> 1), m = cs.m0 + mi, am = m < 0 ? -m : m;
+  const bool row_ok = mi < cs.Mc;
+  for (int kc = rg.x; kc < rg.x + rg.y; ++kc) {
+    const size_t chunk = (size_t)(base + kc) * TC_ACHUNK_FLOATS;
+#pragma unroll 1
+    for (int q = 0; q < TC_CHUNK_K / 4; ++q) {
+      float v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int l = kc * TC_CHUNK_K + 4 * q + i;
+        float x = 0.f;
+        if (row_ok && l < Lb && l >= mp && am <= l) {
+          const float f = __ldg(reinterpret_cast<const float*>(flm + (l * l + l + m)) + (r & 1));
+          x = dq(Q, Lmax, mp, l, m) * f;
+        }
+        v[i] = x;
+      }
+      put_split4(t.hi, t.lo, chunk + (r >> 3) * (TC_CHUNK_K * 8) + q * 32 + (r & 7) * 4, v);
+    }
+  }
+}
+
 }  // namespace tc
 
 // ---------------------------------------------------------------------------
@@ -255,6 +296,20 @@ void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int&
       const int kb = std::max(mp, bmin);
       if (kb >= Lb) continue;
       range[(size_t)mp * ntiles + t] = make_int2(kb / TC_CHUNK_K, nchunk - kb / TC_CHUNK_K);
+    }
+}
+
+void tc_analysis_a_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& nmt) {
+  nmt = (cs.Mc + TC_A_ROWS / 2 - 1) / (TC_A_ROWS / 2);
+  const int nchunk = (Lb + TC_CHUNK_K - 1) / TC_CHUNK_K;
+  range.assign((size_t)Lb * nmt, make_int2(0, 0));
+  for (int mp = 0; mp < Lb; ++mp)
+    for (int t = 0; t < nmt; ++t) {
+      const int mlo = cs.m0 + t * (TC_A_ROWS / 2), mhi = cs.m0 + std::min((t + 1) * (TC_A_ROWS / 2), cs.Mc) - 1;
+      const int amin = (mlo <= 0 && mhi >= 0) ? 0 : std::min(std::abs(mlo), std::abs(mhi));
+      const int kb = std::max(mp, amin);
+      if (kb >= Lb) continue;
+      range[(size_t)mp * nmt + t] = make_int2(kb / TC_CHUNK_K, nchunk - kb / TC_CHUNK_K);
     }
 }
 
@@ -292,18 +347,54 @@ bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int L
   return launch_ok("fill_synthesis_table_kernel");
 }
 
+// The warp-specialised persistent engine is the default; CRV_TC_WS=0 selects the
+// one-tile-per-CTA form (two CTAs per SM), kept for comparison.
+static bool use_ws() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("CRV_TC_WS");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v == 1;
+}
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
-                 int* err, cudaStream_t st) {
+                 int* err, int* ctr, cudaStream_t st, TcATab ta) {
   tc::AnalysisProb pb{Q32, Lmax, flm, tb, Lb, cs, X};
   dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
+  if (ta.hi && use_ws()) {
+    // A operand into its tables first (one pass over Delta and f), then both operands by copy
+    {
+      KTimer kt(K_TC_A, st);
+      tc::fill_analysis_a_kernel<<<dim3(ta.nmt, Lb), TC_A_ROWS, 0, st>>>(Q32, Lmax, flm, Lb, cs, ta);
+      kt.done();
+      if (!launch_ok("fill_analysis_a_kernel")) return false;
+    }
+    tc::AnalysisProbA pa;
+    static_cast<tc::AnalysisProb&>(pa) = pb;
+    pa.ta = ta;
+    return launch_tc_gemm_ws<tc::AnalysisProbA, tc::BNC>(pa, grid, sm_count(), ctr, err, st, K_TC_A);
+  }
+  if (use_ws()) return launch_tc_gemm_ws<tc::AnalysisProb, tc::BNC>(pb, grid, sm_count(), ctr, err, st, K_TC_A);
   return launch_tc_gemm<tc::AnalysisProb, tc::BNC>(pb, grid, err, st, K_TC_A);
 }
 
 bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
-                  cx<double>* flm, int* err, cudaStream_t st) {
+                  cx<double>* flm, int* err, int* ctr, cudaStream_t st) {
   tc::SynthesisProb pb{Y, tb, Lb, cs, Zscratch};
   dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
-  if (!launch_tc_gemm<tc::SynthesisProb, tc::BNC>(pb, grid, err, st, K_TC_S)) return false;
+  const bool ok = use_ws() ? launch_tc_gemm_ws<tc::SynthesisProb, tc::BNC>(pb, grid, sm_count(), ctr, err, st, K_TC_S)
+                           : launch_tc_gemm<tc::SynthesisProb, tc::BNC>(pb, grid, err, st, K_TC_S);
+  if (!ok) return false;
   dim3 g2((Lb + 255) / 256, cs.Mc);
   KTimer kt(K_TC_S, st);
   tc::synth_reduce_kernel<<<g2, 256, 0, st>>>(Q32, Lmax, Zscratch, Lb, cs, flm);

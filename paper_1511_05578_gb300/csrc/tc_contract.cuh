@@ -26,8 +26,24 @@ struct TcTab {
 };
 constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 16, TC_CHUNK_FLOATS = TC_TILE_ROWS * TC_CHUNK_K;
 
+// Per-map A operand of the analysis contraction for one scale (rebuilt for every map and
+// scale): for every (m', m-tile of 64 values of m) the run of 16-wide K chunks from
+// l = max(m', min |m| of the tile) on, each chunk a 128-row x 16 block (rows (m, Re|Im),
+// value Delta^l_{m'm} f_lm) in an engine stage's layout, split into TF32 hi and lo. Chunk
+// kc of (m', mt) sits at hi/lo + (base[m' * nmt + mt] + kc) * TC_ACHUNK_FLOATS.
+constexpr int TC_A_ROWS = 128, TC_ACHUNK_FLOATS = TC_A_ROWS * TC_CHUNK_K;
+struct TcATab {
+  float* hi = nullptr;
+  float* lo = nullptr;
+  const long long* base = nullptr;
+  const int2* range = nullptr;
+  int nmt = 0;
+};
+
 // Chunk ranges per (m', tile), m' < Lb (host).
 void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
+// Chunk ranges of the per-map A tables per (m', m-tile) (host).
+void tc_analysis_a_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& nmt);
 void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
 // Fill a table (device); t.base / t.range already on the device.
 bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
@@ -35,9 +51,11 @@ bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb
 bool tc_fill_synthesis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
                              float* lo, cudaStream_t st);
 
+// err: device error flag (bounded waits); ctr: a device int for the tile counter of the
+// persistent engine (the plan's, one stream at a time).
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
-                 int* err, cudaStream_t st);
+                 int* err, int* ctr, cudaStream_t st, TcATab ta = TcATab());
 bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
-                  cx<double>* flm, int* err, cudaStream_t st);
+                  cx<double>* flm, int* err, int* ctr, cudaStream_t st);
 
 }  // namespace crv

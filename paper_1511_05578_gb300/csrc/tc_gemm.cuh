@@ -1,15 +1,19 @@
 // tcgen05 split-FP32 GEMM engine (sm_103a) of the Delta contractions of the mixed path.
 //
 // D[128 x BN] = sum_k A[128 x k] B[BN x k]^T with FP32 operands produced on the fly by a
-// problem object. Each operand x is split into TF32 hi = rna(x), lo = rna(x - hi); a
-// K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM accumulator (split-FP32,
-// ~2^-22 per product). All 256 threads build the operand stage in shared memory in the
-// canonical K-major no-swizzle layout (8-row x 16-byte core matrices), double-buffered,
-// with the next chunk's loads in flight; one thread issues tcgen05.mma and commits to the
-// stage's mbarrier; waits are bounded and set an error flag instead of hanging; all
-// warps drain TMEM with tcgen05.ld. Stages of K = 16 keep a CTA at ~98 KB of shared
-// memory and 256 TMEM columns, so two CTAs share an SM and one's prologue and epilogue
-// overlap the other's MMAs.
+// problem object or copied from pre-split tables. Each operand x is split into TF32
+// hi = rna(x), lo = rna(x - hi); a K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM
+// accumulator (split-FP32, ~2^-22 per product). Operand stages sit in shared memory in the
+// canonical K-major no-swizzle layout (8-row x 16-byte core matrices); one thread issues
+// tcgen05.mma and commits to mbarriers; every wait is bounded and sets an error flag
+// instead of hanging; TMEM is drained with tcgen05.ld. Two forms:
+//   tc_gemm_kernel     one output tile per CTA, all 256 threads build the operands, two
+//                      stages, two CTAs per SM (one's prologue and epilogue overlap the
+//                      other's MMAs);
+//   tc_gemm_ws_kernel  persistent and warp-specialised, one CTA per SM: operand producers
+//                      (or bulk copies of pre-split tables), a copy lane, an MMA lane and
+//                      epilogue warps around a four-stage ring and two TMEM accumulators,
+//                      tiles taken in order from a global counter.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -59,8 +63,11 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
   return r;
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count = 1) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
@@ -136,7 +143,7 @@ __device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a
 
 // ---------------------------------------------------------------------------
 // The GEMM kernel: one 128 x BN output tile per CTA.
-//   Prob::tile(z, r0, c0, kb, ke)             tile coordinates and K range from blockIdx
+//   Prob::tile(bx, by, bz, z, r0, c0, kb, ke) tile coordinates and K range of tile (bx, by, bz)
 //   Prob::a4(z, r0, k0, r, q, x[4])           A[r0 + r][k0 + 4q .. +3]
 //   Prob::store16(z, r0, c0, r, cc, d[16])    D[r0 + r][c0 + cc .. +15] (all 32 lanes call it)
 //   Prob::zero16(z, r0, c0, r, cc)            same for a tile with an empty K range
@@ -148,6 +155,9 @@ __device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a
 // ---------------------------------------------------------------------------
 template <class P, class = void> struct BulkB { static constexpr bool value = false; };
 template <class P> struct BulkB<P, std::enable_if_t<P::kBulkB>> { static constexpr bool value = true; };
+// Prob::kBulkA (persistent engine only): the A tiles are also in tables, Prob::a_tiles(z, r0, k0, hi, lo)
+template <class P, class = void> struct BulkA { static constexpr bool value = false; };
+template <class P> struct BulkA<P, std::enable_if_t<P::kBulkA>> { static constexpr bool value = true; };
 template <class Prob, int BN>
 __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   using G = Geo<BN>;
@@ -162,7 +172,7 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   const int tid = threadIdx.x, warp = tid >> 5;
 
   int mp, r0, c0g, kb, ke;
-  pb.tile(mp, r0, c0g, kb, ke);
+  pb.tile(blockIdx.x, blockIdx.y, blockIdx.z, mp, r0, c0g, kb, ke);
   const int nchunks = (ke > kb) ? (ke - kb + BK - 1) / BK : 0;
 
   if (tid == 0) {
@@ -305,6 +315,284 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent form of the same GEMM (one CTA per SM, 704 threads):
+//   warps 0-15 build the A operand of each K chunk (two chunks of loads in flight per
+//              thread; four warps per scheduler hide each other's latency) into a ring of
+//              WS_STAGES stages and arrive on the stage's a_full;
+//              thread 0 also takes the CTA's next tile from a global counter (tiles in the
+//              order x fastest, then y, then z, so that the CTAs of the GPU work on
+//              neighbouring tiles at any time and share the B chunks and Delta rows in L2)
+//              and posts it in a small ring of tile indices;
+//   warp 16    (one lane) bulk-copies the pre-split B tiles into the ring, up to
+//              WS_STAGES chunks ahead, completing on b_full;
+//   warp 17    (one lane) issues the MMAs of a stage once both halves have landed, commits
+//              to the stage's empty barrier, and after a tile's last chunk to acc_full;
+//   warps 18-21 drain the accumulator of the previous tile (two TMEM accumulators of BN
+//              columns alternate), then arrive on acc_empty.
+// Every mbarrier wait is bounded and made by one lane whose result the warp shares, so
+// lanes never disagree; a role whose wait gives up records the error and stops, the others
+// then give up in turn, and B copies still in flight are waited for before the CTA exits.
+// The producer warps meet at a named barrier once per tile (all of them, on every path).
+// With Prob::kBulkA the A tiles come from tables too: warp 0 only schedules tiles, and the
+// copy lane fetches A and B of a stage together (PW = 1 producer warp, 224 threads).
+// Requires Prob::kBulkB; *ctr must be 0 at launch.
+// ---------------------------------------------------------------------------
+constexpr int WS_STAGES = 4, WS_TRING = 4;
+template <class Prob> struct WsWarps { static constexpr int value = BulkA<Prob>::value ? 1 : 16; };  // producer warps
+template <int BN> struct GeoWS {
+  static constexpr int SMEM_BYTES = WS_STAGES * Geo<BN>::STAGE_BYTES + 1024 + 512;
+  static constexpr uint32_t TMEM_COLS = 2 * Geo<BN>::TMEM_COLS;
+};
+
+template <int PW> __device__ __forceinline__ void producers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(PW * 32) : "memory");
+}
+// Bounded wait by lane 0 of the calling warp, result shared with the warp (all lanes call).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* err) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, err) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+template <class Prob, int BN>
+__global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
+    tc_gemm_ws_kernel(Prob pb, int gx, int gy, int ntiles, int* ctr, int* err) {
+  using G = Geo<BN>;
+  constexpr int B_BYTES = G::B_BYTES, STAGE_BYTES = G::STAGE_BYTES, S = WS_STAGES, D = WS_TRING;
+  constexpr bool BA = BulkA<Prob>::value;
+  constexpr int PW = WsWarps<Prob>::value, WS_WB = PW, WS_WM = PW + 1;
+  static_assert(BulkB<Prob>::value, "the B operand comes from tables");
+  static_assert(GeoWS<BN>::TMEM_COLS <= 512, "two accumulators fit in TMEM");
+  extern __shared__ unsigned char smraw[];
+  const uint32_t raw = smem_u32(smraw);
+  unsigned char* base = smraw + (((raw + 1023u) & ~1023u) - raw);
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(base + S * STAGE_BYTES);
+  uint64_t* b_full = a_full + S;
+  uint64_t* empty = b_full + S;
+  uint64_t* acc_full = empty + S;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* tr_full = acc_empty + 2;
+  uint64_t* tr_empty = tr_full + D;
+  int* tring = reinterpret_cast<int*>(tr_empty + D);
+  int* abort_flag = tring + D;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(abort_flag + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&a_full[i], PW);
+      mbar_init(&b_full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 4);
+    }
+    for (int i = 0; i < D; ++i) {
+      mbar_init(&tr_full[i], 1);
+      mbar_init(&tr_empty[i], 6);  // B producer, MMA issuer, four epilogue warps
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(GeoWS<BN>::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  // tile t -> coordinates and number of K chunks
+  auto tile_of = [&](int t, int& mp, int& r0, int& c0, int& kb, int& nch) {
+    int ke;
+    pb.tile(t % gx, (t / gx) % gy, t / (gx * gy), mp, r0, c0, kb, ke);
+    nch = (ke > kb) ? (ke - kb + BK - 1) / BK : 0;
+  };
+  // consumers: the j-th tile of this CTA from the ring (every lane of the warp gets it)
+  auto next_tile = [&](uint32_t j, int& t) -> bool {
+    const int sl = j % D;
+    if (!warp_wait(&tr_full[sl], (j / D) & 1u, err)) return false;
+    t = tring[sl];
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&tr_empty[sl]);
+    return true;
+  };
+
+  if (warp < PW) {
+    // ---- A producers: thread tid covers row tid % 128 of the A tile, k-quads q = tid / 128 + j * PQ ----
+    constexpr int PQ = BA ? 1 : PW * 32 / BM, NQ = (BK / 4) / PQ;
+    static_assert(BA || NQ * PQ == BK / 4, "producer threads tile the stage");
+    const int pr = tid % BM, pq = tid / BM;
+    uint32_t u = 0;
+    for (uint32_t j = 0;; ++j) {
+      const int sl = j % D;
+      if (tid == 0) {
+        int t = ntiles;  // terminal value on any failure
+        if (!*abort_flag && mbar_wait(&tr_empty[sl], ((j / D) + 1) & 1u, err)) t = min(atomicAdd(ctr, 1), ntiles);
+        else *abort_flag = 1;
+        tring[sl] = t;
+        mbar_arrive(&tr_full[sl]);
+      }
+      __syncwarp();
+      producers_sync<PW>();
+      const int t = tring[sl];  // the same value for every producer thread: all leave together
+      if (t >= ntiles) break;
+      int mp, r0, c0, kb, nch;
+      tile_of(t, mp, r0, c0, kb, nch);
+      if (BA) nch = 0;  // A arrives with B
+      float x0[NQ][4], x1[NQ][4];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (nch > 0) pb.a4(mp, r0, kb, pr, pq + q * PQ, x0[q]);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        if (nch > 1) pb.a4(mp, r0, kb + BK, pr, pq + q * PQ, x1[q]);
+      for (int c = 0; c < nch; ++c, ++u) {
+        float x2[NQ][4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if (c + 2 < nch) pb.a4(mp, r0, kb + (c + 2) * BK, pr, pq + q * PQ, x2[q]);
+        const int s = u % S;
+        if (!warp_wait(&empty[s], ((u / S) + 1) & 1u, err)) {
+          *abort_flag = 1;
+          break;
+        }
+        unsigned char* st = base + s * STAGE_BYTES;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) put4(st, st + A_BYTES, pr, pq + q * PQ, x0[q]);
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a_full[s]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) { x0[q][i] = x1[q][i]; x1[q][i] = x2[q][i]; }
+      }
+      __syncwarp();
+      producers_sync<PW>();  // a failure in any warp (abort_flag) ends the loop at the next tile
+    }
+  } else if (warp == WS_WB) {
+    // ---- B producer ----
+    if (lane == 0) {
+      uint32_t u = 0;
+      int last[S];
+      for (int i = 0; i < S; ++i) last[i] = -1;
+      bool ok = true;
+      for (uint32_t j = 0; ok; ++j) {
+        int t;
+        const int sl = j % D;
+        if (!mbar_wait(&tr_full[sl], (j / D) & 1u, err)) break;
+        t = tring[sl];
+        mbar_arrive(&tr_empty[sl]);
+        if (t >= ntiles) break;
+        int mp, r0, c0, kb, nch;
+        tile_of(t, mp, r0, c0, kb, nch);
+        for (int c = 0; c < nch; ++c, ++u) {
+          const int s = u % S;
+          if (!mbar_wait(&empty[s], ((u / S) + 1) & 1u, err)) { ok = false; break; }
+          unsigned char* st = base + s * STAGE_BYTES;
+          const void *bhi, *blo;
+          pb.b_tiles(mp, c0, kb + c * BK, bhi, blo);
+          if constexpr (BA) {
+            const void *ahi, *alo;
+            pb.a_tiles(mp, r0, kb + c * BK, ahi, alo);
+            mbar_expect_tx(&b_full[s], 2u * (A_BYTES + B_BYTES));
+            bulk_g2s(st, ahi, A_BYTES, &b_full[s]);
+            bulk_g2s(st + A_BYTES, alo, A_BYTES, &b_full[s]);
+          } else {
+            mbar_expect_tx(&b_full[s], 2u * B_BYTES);
+          }
+          bulk_g2s(st + 2 * A_BYTES, bhi, B_BYTES, &b_full[s]);
+          bulk_g2s(st + 2 * A_BYTES + B_BYTES, blo, B_BYTES, &b_full[s]);
+          last[s] = (int)u;
+        }
+      }
+      // copies issued and possibly not consumed (an error elsewhere) land before exit
+      for (int i = 0; i < S; ++i)
+        if (last[i] >= 0) mbar_wait(&b_full[i], ((uint32_t)last[i] / S) & 1u, err);
+    }
+  } else if (warp == WS_WM) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      uint32_t u = 0;
+      bool ok = true;
+      for (uint32_t j = 0; ok; ++j) {
+        const int sl = j % D;
+        if (!mbar_wait(&tr_full[sl], (j / D) & 1u, err)) break;
+        const int t = tring[sl];
+        mbar_arrive(&tr_empty[sl]);
+        if (t >= ntiles) break;
+        int mp, r0, c0, kb, nch;
+        tile_of(t, mp, r0, c0, kb, nch);
+        const uint32_t a = j & 1u;
+        if (!mbar_wait(&acc_empty[a], ((j >> 1) + 1) & 1u, err)) break;
+        fence_after();
+        const uint32_t acc = tmem + a * (uint32_t)BN;
+        for (int c = 0; c < nch; ++c, ++u) {
+          const int s = u % S;
+          if ((!BA && !mbar_wait(&a_full[s], (u / S) & 1u, err)) || !mbar_wait(&b_full[s], (u / S) & 1u, err)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t sa = smem_u32(base + s * STAGE_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < BK / 8; ++ks) {
+            const uint32_t koff = ks * 256;
+            const uint64_t ahi = smem_desc(sa + koff), alo = smem_desc(sa + A_BYTES + koff);
+            const uint64_t bhi = smem_desc(sa + 2 * A_BYTES + koff), blo = smem_desc(sa + 2 * A_BYTES + B_BYTES + koff);
+            mma_tf32(acc, alo, bhi, G::IDESC, (c == 0 && ks == 0) ? 0u : 1u);
+            mma_tf32(acc, ahi, blo, G::IDESC, 1u);
+            mma_tf32(acc, ahi, bhi, G::IDESC, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        if (nch > 0) mma_commit(&acc_full[a]);
+        else mbar_arrive(&acc_full[a]);
+      }
+    }
+  } else {
+    // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. + 31 ----
+    const int lq = warp & 3, r = lq * 32 + lane;
+    for (uint32_t j = 0;; ++j) {
+      int t;
+      if (!next_tile(j, t) || t >= ntiles) break;
+      int mp, r0, c0, kb, nch;
+      tile_of(t, mp, r0, c0, kb, nch);
+      const uint32_t a = j & 1u;
+      if (!warp_wait(&acc_full[a], (j >> 1) & 1u, err)) break;
+      fence_after();
+      for (int cc = 0; cc < BN; cc += 16) {
+        if (nch > 0) {
+          float d[16];
+          tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + a * (uint32_t)BN + (uint32_t)cc, d);
+          pb.store16(mp, r0, c0, r, cc, d);
+        } else {
+          pb.zero16(mp, r0, c0, r, cc);
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
+    }
+  }
+  __syncwarp();
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GeoWS<BN>::TMEM_COLS)
+                 : "memory");
+  }
+}
+
 }  // namespace tc
 
 template <class Prob, int BN>
@@ -318,6 +606,30 @@ bool launch_tc_gemm(const Prob& pb, dim3 grid, int* err, cudaStream_t st, int ki
   }
   KTimer kt(kind, st);
   tc::tc_gemm_kernel<Prob, BN><<<grid, tc::NT, tc::Geo<BN>::SMEM_BYTES, st>>>(pb, err);
+  kt.done();
+  return launch_ok(kind_name(kind));
+}
+
+// Persistent warp-specialised launch over the tiles of grid (one CTA per SM at most);
+// ctr: a device int, zeroed here on the stream before the launch.
+template <class Prob, int BN>
+bool launch_tc_gemm_ws(const Prob& pb, dim3 grid, int nsm, int* ctr, int* err, cudaStream_t st, int kind) {
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(tc::tc_gemm_ws_kernel<Prob, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::GeoWS<BN>::SMEM_BYTES) != cudaSuccess)
+      return false;
+    attr = true;
+  }
+  const long long nt = (long long)grid.x * grid.y * grid.z;
+  if (nt <= 0) return true;
+  if (nt > 0x7fffffffLL) return false;
+  const int ctas = (int)std::min<long long>(nt, nsm);
+  if (cudaMemsetAsync(ctr, 0, sizeof(int), st) != cudaSuccess) return false;
+  KTimer kt(kind, st);
+  constexpr int threads = (tc::WsWarps<Prob>::value + 6) * 32;
+  tc::tc_gemm_ws_kernel<Prob, BN><<<ctas, threads, tc::GeoWS<BN>::SMEM_BYTES, st>>>(pb, (int)grid.x, (int)grid.y,
+                                                                                  (int)nt, ctr, err);
   kt.done();
   return launch_ok(kind_name(kind));
 }
