@@ -556,6 +556,32 @@ static int ring_chunk(crv_plan_s* p, int Lb, size_t elem) {
   return (int)std::max<size_t>(1, std::min<size_t>((size_t)Lb, p->ring_bytes / per));
 }
 
+// Ring steps of the analysis for rings b0 .. b0 + nr - 1 (Eq. inverse_feul over (m, n));
+// Z: unrotated plans, whose columns below nlo and entries |m| > |n| are zero.
+template <class T, class OutT, bool Z>
+static bool ring_inverse(crv_plan_s* p, const FftSet& fs, const ColSet& cs, const cx<T>* Xb, cx<T>* R, OutT* W, int b0,
+                         int nr, int N, int ni0, int Nh, int h0, int nlo, size_t wstride, cudaStream_t st) {
+  const int Nhs = Nh - h0;
+  if (p->real) {
+    // m step on the n >= 0 columns, then the n step with real output, rows in pairs
+    if (Nhs > 0) {
+      LdRingMHalf<T, Z> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nhs, FastDiv((uint32_t)Nhs), h0};
+      StRingMHalf<T> sm{R, N, Nhs, FastDiv((uint32_t)Nhs), Nh, h0};
+      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nhs, lm, sm, st)) return false;
+    }
+    const int npair = (N + 1) / 2;
+    LdRingNHerm<T, Z> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair), nlo};
+    StWRowPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
+    return run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * npair, ln, sw, st);
+  }
+  LdRingN<T, Z> ln{Xb + (size_t)b0 * cs.pitch(), cs, N, FastDiv((uint32_t)cs.Mc), nlo};
+  StContig<T> sc{R, N + 1};
+  if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
+  LdRingM<T> lm{R, cs.Mc, cs.m0, N, N + 1, false, FastDiv((uint32_t)N)};
+  StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false, FastDiv((uint32_t)N)};
+  return run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st);
+}
+
 template <class T, class OutT>
 static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, OutT* W, cudaStream_t st) {
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
@@ -594,28 +620,12 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   const size_t wstride = (size_t)N * N * (p->real ? 1 : 2);
   const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
   // unrotated plans: columns |n| < nlo are zero, so the ring steps skip them (nstep = 1 there)
-  const int nlo = p->unrot ? p->nlo[j] : 0, h0 = std::min(nlo, Nh), Nhs = Nh - h0;
+  const int nlo = p->unrot ? p->nlo[j] : 0, h0 = std::min(nlo, Nh);
   for (int b0 = 0; b0 < Lb; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
-    if (p->real) {
-      // m step on the n >= 0 columns, then the n step with real output, rows in pairs
-      if (Nhs > 0) {
-        LdRingMHalf<T> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nhs, FastDiv((uint32_t)Nhs), h0, p->unrot};
-        StRingMHalf<T> sm{R, N, Nhs, FastDiv((uint32_t)Nhs), Nh, h0};
-        if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * Nhs, lm, sm, st)) return false;
-      }
-      const int npair = (N + 1) / 2;
-      LdRingNHerm<T> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair), nlo};
-      StWRowPair<T, OutT> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
-      if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * npair, ln, sw, st)) return false;
-    } else {
-      LdRingN<T> ln{Xb + (size_t)b0 * cs.pitch(), cs, N, FastDiv((uint32_t)cs.Mc), nlo, p->unrot};
-      StContig<T> sc{R, N + 1};
-      if (!run_rows<T>(K_RING_INV_N, dft_of<T>(fs), +1, nr * cs.Mc, ln, sc, st)) return false;
-      LdRingM<T> lm{R, cs.Mc, cs.m0, N, N + 1, false, FastDiv((uint32_t)N)};
-      StW<T, OutT> sw{W + (size_t)b0 * wstride, N, false, FastDiv((uint32_t)N)};
-      if (!run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st)) return false;
-    }
+    const bool ok = p->unrot ? ring_inverse<T, OutT, true>(p, fs, cs, Xb, R, W, b0, nr, N, ni0, Nh, h0, nlo, wstride, st)
+                             : ring_inverse<T, OutT, false>(p, fs, cs, Xb, R, W, b0, nr, N, ni0, Nh, h0, nlo, wstride, st);
+    if (!ok) return false;
   }
   return true;
 }

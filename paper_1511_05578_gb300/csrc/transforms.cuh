@@ -164,11 +164,11 @@ struct PairMap {
 
 
 // Ring inverse, step over n: sequence (b, mi) of the planes Xb[b] -> T[b][mi][g].
-template <class T>
+// Z (unrotated curvelets): columns |n| < nlo and |m| > |n| are zero and are not read.
+template <class T, bool Z = false>
 struct LdRingN {
   const cx<T>* Xb; ColSet cs; int N; FastDiv fMc;
-  int nlo = 0;         // columns |n| < nlo are zero (and not read)
-  bool mzero = false;  // columns |m| > |n| are zero (unrotated curvelets)
+  int nlo = 0;
   __device__ cx<T> operator()(int c, int j) const {
     const int b = (int)fMc.div((uint32_t)c), mi = c - b * cs.Mc;
     // j = n mod N; find ni with n0 + nstep*ni == n
@@ -177,8 +177,10 @@ struct LdRingN {
     if (d < 0 || (d & (cs.nstep - 1))) return mk<T>(0, 0);
     const int ni = d >> (cs.nstep - 1);
     if (ni >= cs.Nc) return mk<T>(0, 0);
-    const int an = n < 0 ? -n : n, m = cs.m0 + mi;
-    if (an < nlo || (mzero && (m < 0 ? -m : m) > an)) return mk<T>(0, 0);
+    if constexpr (Z) {
+      const int an = n < 0 ? -n : n, m = cs.m0 + mi;
+      if (an < nlo || (m < 0 ? -m : m) > an) return mk<T>(0, 0);
+    }
     return Xb[(size_t)b * cs.pitch() + cs.col(mi, ni)];
   }
 };
@@ -299,15 +301,15 @@ template <class T> struct Mirror<StRingNPair<T>> { static constexpr int value = 
 // ---------------------------------------------------------------------------
 // Analysis, step over m (sign +1) for n >= 0: column (b, h) of Xb[b][mi][ni], extended to
 // m < 0 by the conjugate of the -n column -> R[b][a][h].
-template <class T>
+// Z (unrotated curvelets): the columns start at h0, and entries |m| > n are zero and not read.
+template <class T, bool Z = false>
 struct LdRingMHalf {
   const cx<T>* Xb; ColSet cs; int ni0, N, Nh; FastDiv fNh;  // Nh columns per ring, from h0 on
-  int h0 = 0;          // first column transformed
-  bool mzero = false;  // entries |m| > n are zero and not read (unrotated curvelets)
+  int h0 = 0;
   __device__ const cx<T>* at(int c, int j, int& m, bool& z) const {
-    const int b = (int)fNh.div((uint32_t)c), h = h0 + (c - b * Nh), ni = ni0 + h;
+    const int b = (int)fNh.div((uint32_t)c), h = (Z ? h0 : 0) + (c - b * Nh), ni = ni0 + h;
     m = (j <= (N - 1) / 2) ? j : j - N;
-    z = mzero && (m < 0 ? -m : m) > h * cs.nstep;
+    z = Z && (m < 0 ? -m : m) > h * cs.nstep;
     const cx<T>* base = Xb + (size_t)b * cs.pitch();
     return m >= 0 ? base + cs.col(m, ni) : base + cs.col(-m, cs.Nc - 1 - ni);
   }
@@ -337,15 +339,16 @@ struct StRingMHalf {  // R[b][a][h0 + h], rows of Rp columns; Nh columns per rin
 // Analysis, step over n (sign +1) with real output: rows a1 = 2 ap and a2 = 2 ap + 1 of
 // R[b][a][h], each extended Hermitian in n (n < 0: conjugate of -n), packed as x + i y;
 // the transform's real and imaginary parts are the two rows of W.
-template <class T>
+// Z (unrotated curvelets): |n| < nlo is zero (those columns of R are not written).
+template <class T, bool Z = false>
 struct LdRingNHerm {
   const cx<T>* R; int N, Nh, nstep, npair; FastDiv fP;
-  int nlo = 0;  // |n| < nlo: zero (those columns of R are not written)
+  int nlo = 0;
   __device__ cx<T> operator()(int c, int j) const {
     const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair), a2 = a1 + 1;
     const int n = (j <= (N - 1) / 2) ? j : j - N;
     const int an = n < 0 ? -n : n;
-    if ((an & (nstep - 1)) || an < nlo) return mk<T>(0, 0);
+    if ((an & (nstep - 1)) || (Z && an < nlo)) return mk<T>(0, 0);
     const int h = an >> (nstep - 1);
     const cx<T>* rb = R + (size_t)b * N * Nh;
     cx<T> x = rb[(size_t)a1 * Nh + h];
@@ -357,7 +360,7 @@ struct LdRingNHerm {
     const int b = (int)fP.div((uint32_t)c), a1 = 2 * (c - b * npair);
     const int n = (j <= (N - 1) / 2) ? j : j - N;
     const int an = n < 0 ? -n : n;
-    if ((an & (nstep - 1)) || an < nlo) return;
+    if ((an & (nstep - 1)) || (Z && an < nlo)) return;
     const cx<T>* q = R + (size_t)b * N * Nh + (size_t)a1 * Nh + (an >> (nstep - 1));
     pf_l1(q);
     if (a1 + 1 < N) pf_l1(q + Nh);
