@@ -115,6 +115,12 @@ int crv_plan_info(crv_plan_t plan, int* J, int* Lj, size_t* w_elems, int* L_phi,
  * invalid). Clears the condition. */
 int crv_plan_check(crv_plan_t plan);
 
+/* Self-test of that error path: launch, on the stream, one thread that waits on a device
+ * barrier nothing arrives at, giving up after `polls` polls (1 <= polls <= 1e6) as every
+ * bounded wait of the library does; the next crv_plan_check then returns CRV_ETIMEOUT.
+ * Makes no other device work, leaves nothing in flight; CRV_EINVAL for a bad argument. */
+int crv_debug_bounded_wait(crv_plan_t plan, long polls, void* stream);
+
 /* Host copy of plan tables, for inspection and tests.
  *   crv_plan_kernel:  psi[l][n + L_j - 1] = sPsi^(j)_ln (real, Eq. wav_factorized), l < L_j
  *   crv_plan_scaling: phi[l] = sqrt(4pi/(2l+1)) Phi_l0 = sqrt(k_lambda(l/lambda^J0)), l < L

@@ -1085,6 +1085,12 @@ int crv_plan_check(crv_plan_t p) {
   return CRV_OK;
 }
 
+int crv_debug_bounded_wait(crv_plan_t p, long polls, void* stream) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (polls < 1 || polls > 1000000) return fail(CRV_EINVAL, "polls must be in [1, 1e6]");
+  return tc_bounded_wait_probe(p->d_err, polls, (cudaStream_t)stream) ? CRV_OK : CRV_ECUDA;
+}
+
 int crv_plan_kernel(crv_plan_t p, int j, double* out) {
   if (!p || !out) return fail(CRV_EINVAL, "null argument");
   if (j < p->J0 || j > p->J) return fail(CRV_EINVAL, "scale out of range");

@@ -402,4 +402,10 @@ bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int 
   return launch_ok("synth_reduce_kernel");
 }
 
+bool tc_bounded_wait_probe(int* err, long polls, cudaStream_t st) {
+  tc::bounded_wait_probe_kernel<<<1, 32, 0, st>>>(err, polls);
+  count_launch();
+  return launch_ok("bounded_wait_probe_kernel");
+}
+
 }  // namespace crv

@@ -57,5 +57,7 @@ bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int
                  int* err, int* ctr, cudaStream_t st, TcATab ta = TcATab());
 bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int Lb, ColSet cs, cx<float>* Zscratch,
                   cx<double>* flm, int* err, int* ctr, cudaStream_t st);
+// One thread waits on an mbarrier nothing arrives at, `polls` polls at most, and sets *err.
+bool tc_bounded_wait_probe(int* err, long polls, cudaStream_t st);
 
 }  // namespace crv

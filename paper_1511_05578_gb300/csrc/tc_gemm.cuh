@@ -78,8 +78,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  for (long it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, long limit = kWaitLimit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicExch(err, 1);
   return false;
@@ -591,6 +591,17 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GeoWS<BN>::TMEM_COLS)
                  : "memory");
   }
+}
+
+// Self-test of the error path of the bounded waits: one thread waits on an mbarrier that
+// nothing arrives at, with a limit of `limit` polls; the wait gives up and sets *err. No
+// other thread, copy or MMA is involved, so nothing is left in flight.
+__global__ void bounded_wait_probe_kernel(int* err, long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(&bar, 0u, err, limit);
 }
 
 }  // namespace tc
