@@ -15,6 +15,35 @@ struct __align__(2 * sizeof(T)) cx {
 template <class T> __host__ __device__ __forceinline__ cx<T> mk(T a, T b) { cx<T> r; r.re = a; r.im = b; return r; }
 template <class T> __host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
 template <class T> __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+// FP32 complex addition and subtraction on the device as one paired instruction each
+// (add.rn.f32x2 / sub.rn.f32x2 of sm_100 and later: IEEE round-to-nearest per component,
+// the same results as two scalar operations, half the issue slots).
+__host__ __device__ __forceinline__ cx<float> operator+(cx<float> a, cx<float> b) {
+#ifdef __CUDA_ARCH__
+  uint64_t x, y, z;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.re), "f"(a.im));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.re), "f"(b.im));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+  cx<float> r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.re), "=f"(r.im) : "l"(z));
+  return r;
+#else
+  return mk(a.re + b.re, a.im + b.im);
+#endif
+}
+__host__ __device__ __forceinline__ cx<float> operator-(cx<float> a, cx<float> b) {
+#ifdef __CUDA_ARCH__
+  uint64_t x, y, z;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.re), "f"(a.im));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.re), "f"(b.im));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+  cx<float> r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.re), "=f"(r.im) : "l"(z));
+  return r;
+#else
+  return mk(a.re - b.re, a.im - b.im);
+#endif
+}
 template <class T> __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
   return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
 }

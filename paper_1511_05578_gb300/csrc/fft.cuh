@@ -10,6 +10,8 @@
 // around them need no reordering. Stage 0 has radix R0 = 2^(p mod 4) (16 when 4 | p)
 // and no twiddles; every later stage has radix 16 and builds its twiddles from four
 // table values per thread.
+// FP32 complex additions run as paired f32x2 instructions (common.cuh); additions of an
+// operand rotated by +-i stay scalar (add_rot, sub_rot), so no component swap is needed.
 // Between two stages the values pass once through shared memory. Indices there are
 // padded by one element every 16, which leaves the exchanges of the P = 4096 transform
 // free of bank conflicts. Two exchange buffers alternate, so one barrier per exchange
@@ -69,8 +71,13 @@ struct XBuf2 {
   }
 };
 
-template <int DIR, class T> __device__ __forceinline__ cx<T> rot(cx<T> a) {  // a * (DIR i)
-  return DIR < 0 ? mk(a.im, -a.re) : mk(-a.im, a.re);
+// a + d (DIR i) and a - d (DIR i) as scalar operations: a rotated operand would need its
+// components swapped to take part in a paired (f32x2) addition.
+template <int DIR, class T> __device__ __forceinline__ cx<T> add_rot(cx<T> a, cx<T> d) {
+  return DIR < 0 ? mk(a.re + d.im, a.im - d.re) : mk(a.re - d.im, a.im + d.re);
+}
+template <int DIR, class T> __device__ __forceinline__ cx<T> sub_rot(cx<T> a, cx<T> d) {
+  return DIR < 0 ? mk(a.re - d.im, a.im + d.re) : mk(a.re + d.im, a.im - d.re);
 }
 template <int DIR, class T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, T c, T s) {  // a * (c + DIR i s)
   const T ss = DIR < 0 ? -s : s;
@@ -78,15 +85,20 @@ template <int DIR, class T> __device__ __forceinline__ cx<T> cmulc(cx<T> a, T c,
 }
 
 // 4-point DFT in place, natural order, w = e^{DIR 2 pi i/4}; inputs NZ..3 are zero.
-template <int DIR, int NZ, class T>
+// R2: the input x2 arrives unrotated and is taken as x2 (DIR i).
+template <int DIR, int NZ, class T, bool R2 = false>
 __device__ __forceinline__ void dft4(cx<T>& x0, cx<T>& x1, cx<T>& x2, cx<T>& x3) {
   if constexpr (NZ == 1) {
     x1 = x0; x2 = x0; x3 = x0;
   } else {
     cx<T> s0, d0, s1, d1;
-    if constexpr (NZ == 2) { s0 = x0; d0 = x0; s1 = x1; d1 = rot<DIR>(x1); }
-    else { s0 = x0 + x2; d0 = x0 - x2; s1 = x1 + x3; d1 = rot<DIR>(x1 - x3); }
-    x0 = s0 + s1; x2 = s0 - s1; x1 = d0 + d1; x3 = d0 - d1;
+    if constexpr (NZ == 2) { s0 = x0; d0 = x0; s1 = x1; d1 = x1; }
+    else {
+      if constexpr (R2) { s0 = add_rot<DIR>(x0, x2); d0 = sub_rot<DIR>(x0, x2); }
+      else { s0 = x0 + x2; d0 = x0 - x2; }
+      s1 = x1 + x3; d1 = x1 - x3;
+    }
+    x0 = s0 + s1; x2 = s0 - s1; x1 = add_rot<DIR>(d0, d1); x3 = sub_rot<DIR>(d0, d1);
   }
 }
 
@@ -101,10 +113,10 @@ __device__ __forceinline__ void dft8(cx<T> (&x)[8]) {
     else { a[r] = x[r]; b[r] = x[r]; }
   }
   b[1] = cmulc<DIR>(b[1], c, c);
-  b[2] = rot<DIR>(b[2]);
+  // b[2] (twiddle DIR i) is rotated inside the second 4-point DFT
   b[3] = cmulc<DIR>(b[3], -c, c);
   dft4<DIR, 4>(a[0], a[1], a[2], a[3]);
-  dft4<DIR, 4>(b[0], b[1], b[2], b[3]);
+  dft4<DIR, 4, T, true>(b[0], b[1], b[2], b[3]);
 #pragma unroll
   for (int k = 0; k < 4; ++k) { x[2 * k] = a[k]; x[2 * k + 1] = b[k]; }
 }
@@ -121,13 +133,15 @@ __device__ __forceinline__ void dft16(cx<T> (&x)[16]) {
   x[9] = cmulc<DIR>(x[9], c2, c2);      // 2
   x[13] = cmulc<DIR>(x[13], s1, c1);    // 3
   x[6] = cmulc<DIR>(x[6], c2, c2);      // 2
-  x[10] = rot<DIR>(x[10]);              // 4
+  // x[10] (twiddle w16^4 = DIR i) is rotated inside the row-2 4-point DFT below
   x[14] = cmulc<DIR>(x[14], -c2, c2);   // 6
   x[7] = cmulc<DIR>(x[7], s1, c1);      // 3
   x[11] = cmulc<DIR>(x[11], -c2, c2);   // 6
   x[15] = cmulc<DIR>(x[15], -c1, -s1);  // 9
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4<DIR, 4>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  dft4<DIR, 4>(x[0], x[1], x[2], x[3]);
+  dft4<DIR, 4>(x[4], x[5], x[6], x[7]);
+  dft4<DIR, 4, T, true>(x[8], x[9], x[10], x[11]);
+  dft4<DIR, 4>(x[12], x[13], x[14], x[15]);
   // X[k1 + 4 k2] sits at x[4 k1 + k2]
   cx<T> y[16];
 #pragma unroll
