@@ -82,6 +82,8 @@ class Scheduler:
     """Admission and accounting. The executor provides:
         plan_bytes(key) -> bytes a new plan instance of this key would hold
         create_plan(key) -> plan object (or raises ValueError with a reason when unsupported)
+        destroy_plan(plan)                 frees a plan instance (idle plans are evicted, largest
+                                           first, when a request would not fit otherwise)
         start(req, plan) -> handle;  done(handle) -> bool;  finish(handle) -> result
         now() -> seconds
     """
@@ -97,6 +99,7 @@ class Scheduler:
         self.running = []                  # (req, plan_entry, handle, bytes)
         self.done = []
         self.rejected = []
+        self.evicted = 0                   # idle plan instances freed to admit a request
 
     def _idle_plan(self, key):
         for e in self.plans.get(key, []):
@@ -115,7 +118,11 @@ class Scheduler:
         if need > self.budget and not self.running:
             req.status, req.reason = "rejected", f"needs {need / 1e9:.1f} GB, budget {self.budget / 1e9:.1f} GB"
             return "rejected"
-        if len(self.running) >= self.max_running or self.used + need > self.budget:
+        if len(self.running) >= self.max_running:
+            return "wait"
+        if self.used + need > self.budget and not self._evict_idle(need, keep=e):
+            # resident idle plans freed and it still does not fit: wait for running requests
+            # (it fits alone, since need <= budget)
             return "wait"
         if e is None:
             try:
@@ -131,6 +138,23 @@ class Scheduler:
         req.status, req.start = "running", self.ex.now()
         self.running.append((req, e, self.ex.start(req, e[0]), rb))
         return "started"
+
+    def _evict_idle(self, need, keep=None):
+        """Free idle plan instances (largest first; never `keep`) until `need` more bytes fit.
+        Returns whether they fit."""
+        destroy = getattr(self.ex, "destroy_plan", None)
+        if destroy is None:
+            return False
+        idle = [(k, e) for k, lst in self.plans.items() for e in lst if not e[1] and e is not keep]
+        idle.sort(key=lambda ke: -self.ex.plan_bytes(ke[0]))
+        for k, e in idle:
+            if self.used + need <= self.budget:
+                break
+            self.plans[k].remove(e)
+            destroy(e[0])
+            self.used -= self.ex.plan_bytes(k)
+            self.evicted += 1
+        return self.used + need <= self.budget
 
     def submit(self, req):
         self.queue.append(req)
@@ -171,7 +195,7 @@ class Scheduler:
         lat = [r.finish - r.arrival for r in self.done]
         maps = sum(r.B for r in self.done)
         out = {"requests_done": len(self.done), "requests_rejected": len(self.rejected), "maps_done": maps,
-               "maps_per_s": maps / wall_s if wall_s > 0 else 0.0}
+               "maps_per_s": maps / wall_s if wall_s > 0 else 0.0, "plans_evicted": self.evicted}
         if lat:
             out.update({"p50_ms": 1e3 * percentile(lat, 50), "p99_ms": 1e3 * percentile(lat, 99),
                         "mean_ms": 1e3 * sum(lat) / len(lat)})
@@ -232,10 +256,14 @@ class CudaExecutor:
             return self._plan_bytes[key]
         L, spin, mixed = key
         # estimate before the first instance exists (the plan's own count replaces it once one
-        # does): Delta tables (FP64, + FP32 and the tensor-core tables when mixed) and the two
-        # (m, n, m') workspaces, complex, m over 2L - 1 values for spin != 0
+        # does): Delta tables (FP64, + FP32, the tensor-core B tables of both directions and the
+        # per-map A tables when mixed) and the two (m, n, m') workspaces, complex, m over
+        # 2L - 1 values for spin != 0
         mc = L if spin == 0 else 2 * L - 1
-        return L ** 3 * (8 + (12 if mixed else 0)) + 2 * L * mc * L * (8 if mixed else 16)
+        return L ** 3 * (8 + (26 if mixed else 0)) * (mc // L) + 2 * L * mc * L * (8 if mixed else 16)
+
+    def destroy_plan(self, plan):
+        plan.close()
 
     def create_plan(self, key):
         L, spin, mixed = key

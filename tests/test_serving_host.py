@@ -13,6 +13,7 @@ class FakeExecutor:
     def __init__(self):
         self.t = 0.0
         self.created = []
+        self.destroyed = []
 
     def plan_bytes(self, key):
         return key[0] ** 2
@@ -22,6 +23,9 @@ class FakeExecutor:
             raise ValueError("unsupported")
         self.created.append(key)
         return object()
+
+    def destroy_plan(self, plan):
+        self.destroyed.append(plan)
 
     def start(self, req, plan):
         return {"end": self.t + req.B * req.L / 1000.0, "rid": req.rid}
@@ -119,3 +123,19 @@ def test_w_bytes_matches_grid_sizes():
     Ls = [8, 16, 32, 64, 128, 256, 512, 1024, 1024]
     assert S.w_bytes(1024, 0) == sum(Lb * (2 * Lb - 1) ** 2 * 4 for Lb in Ls)
     assert S.w_bytes(1024, 2) == 2 * S.w_bytes(1024, 0)
+
+
+def test_idle_resident_plans_are_evicted_when_a_request_would_not_fit():
+    """Plans stay resident after their requests; a request of another band limit that fits only
+    without them frees the idle ones instead of waiting for ever."""
+    ex = FakeExecutor()
+    a, b = _req(0, 64), _req(1, 96, t=0.5)
+    budget = max(S.request_bytes(a) + 64 ** 2, S.request_bytes(b) + 96 ** 2) + 10
+    assert S.request_bytes(a) + 64 ** 2 + S.request_bytes(b) + 96 ** 2 > budget
+    sch = S.Scheduler(ex, budget, max_running=4)
+    S.run(sch, [a, b])
+    assert len(sch.done) == 2 and not sch.rejected
+    assert sch.evicted == 1 and len(ex.destroyed) == 1
+    assert b.start >= a.finish
+    assert sch.used == 96 ** 2  # only b's plan stays resident
+    assert sch.stats(1.0)["plans_evicted"] == 1
