@@ -258,6 +258,29 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks, known to every rank (x itself when world == 1): the
+    whole-job time of a replicated run is that of its slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, maps_per_rank, steps, t_ms):
+    """Maps per second of the whole job: every rank's maps over the max-over-ranks time."""
+    return world * maps_per_rank * steps / (t_ms / 1000.0)
+
+
+def rank_map_seeds(rank, B):
+    """Seeds of a rank's B maps: ranks draw disjoint maps of the same distribution."""
+    from paper_1511_05578_gb300 import inputs
+    return [inputs.seed_for(2, rank * B + b) for b in range(B)]
+
+
 def run_reference(args, rank, world):
     # the oracle runs on rank 0 only
     if rank != 0:
@@ -323,8 +346,8 @@ def main():
         # seeded inputs: f_lm on the host -> maps through our inverse SHT (not timed)
         maps = torch.empty((B, L, 2 * L - 1), dtype=torch.float64, device="cuda")
         f1 = plan.flm_tensor(1)
-        for b in range(B):
-            f1.copy_(torch.from_numpy(inputs.flm_gaussian(L, inputs.seed_for(2, rank * B + b), real=True)[None]))
+        for b, seed in enumerate(rank_map_seeds(rank, B)):
+            f1.copy_(torch.from_numpy(inputs.flm_gaussian(L, seed, real=True)[None]))
             crv.crv_sht_inv(plan.handle, f1, maps[b:b + 1], 1, stream.cuda_stream)
         out = torch.empty_like(maps)
         W = plan.W_tensors(1)
@@ -383,13 +406,9 @@ def main():
         n, t = crv.crv_profile_read(k)
         if n:
             kind_ms[name], kind_n[name] = t, n
-    t_max = ms_total
-    if world > 1:
-        tt = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(ms_total, world, "cuda")
     ms_per_step = t_max / args.steps
-    value = world * B * args.steps / (t_max / 1000.0)
+    value = whole_job_rate(world, B, args.steps, t_max)
 
     # per-map latency (p50 / p99) from the per-map events of the timed steps
     lat_ms = sorted(a.elapsed_time(b_) for a, b_ in per_map)
@@ -413,13 +432,10 @@ def main():
                 crv.crv_synthesis(plan.handle, W, Wphi, dev_out, 1, stream.cuda_stream)
                 host_out[b:b + 1].copy_(dev_out, non_blocking=True)
         stream.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
         nb = B * L * (2 * L - 1) * 8
-        e2e = {"value": world * B / t_e2e, "unit": "maps/s", "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+        e2e = {"value": whole_job_rate(world, B, 1, 1000.0 * t_e2e), "unit": "maps/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
 
     # plain FP64 GPU path on a sample of maps, for the mixed/FP64 speedup
     fp64 = None
