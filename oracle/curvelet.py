@@ -16,7 +16,7 @@ from . import build as _build
 __all__ = [
     "lib", "mw_theta", "mw_phi", "half_angles", "wigner_d_factsum", "wigner_d_lrec",
     "risbo_matrix", "delta_matrix", "quad_weight", "sht_inverse", "sht_forward",
-    "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "zeta_unrotated", "psi",
+    "s_lambda", "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "zeta_unrotated", "psi",
     "euler_matrix", "euler_angles", "analysis_point", "analysis_rings", "analysis_from_flm", "analysis", "scaling_map", "wigner_forward_Y",
     "wigner_forward_coeffs", "synthesis_flm", "synthesis", "MUTATION",
 ]
@@ -56,6 +56,8 @@ def lib():
         h.orc_k_diff.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         h.orc_k_lambda.restype = ctypes.c_double
         h.orc_k_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
+        h.orc_s_lambda.restype = ctypes.c_double
+        h.orc_s_lambda.argtypes = [ctypes.c_double, ctypes.c_double]
         _lib = h
     return _lib
 
@@ -192,6 +194,15 @@ def sht_forward(fmap, L, s):
 # --------------------------------------------------------------------------
 # Curvelet construction (Sec. II-B)
 # --------------------------------------------------------------------------
+def s_lambda(lam, t):
+    """s_lambda(t) = s(2 lam/(lam-1) (t - 1/lam) - 1) with s(t) = exp(-1/(1-t^2)) on
+    (-1, 1) and 0 elsewhere (Sec. II-B): the bump whose square, weighted by 1/t,
+    k_lambda integrates."""
+    h = lib()
+    t = np.asarray(t, dtype=np.float64)
+    return np.vectorize(lambda x: h.orc_s_lambda(float(lam), float(x)), otypes=[np.float64])(t)
+
+
 def k_lambda(lam, t):
     """k_lambda(t) (Sec. II-B): normalised integral of s_lambda^2(t')/t' from t to 1."""
     h = lib()

@@ -444,6 +444,9 @@ double orc_k_diff(double lam, double a, double b) {
   return integrate_k(lam, lo, hi) / integrate_k(lam, 1.0 / lam, 1.0);
 }
 
+/* s_lambda(t) itself (Sec. II-B), exported for the pins of the radial kernel. */
+double orc_s_lambda(double lam, double t) { return s_lambda(lam, t); }
+
 double orc_k_lambda(double lam, double t) {
   if (t < 1.0 / lam) return 1.0;
   if (t >= 1.0) return 0.0;

@@ -48,9 +48,8 @@ def test_kernel_support_peak_and_admissibility(lam, J0, L):
         k = O.kappa(lam, j, L)
         inside = (l > lam ** (j - 1)) & (l < lam ** (j + 1))
         assert np.all(k[~inside] == 0.0)
-        # inside the open support kappa > 0 up to rounding (the bump is flat to
-        # ~1e-16 next to its ends)
-        assert np.all(k[inside] >= 0.0) and (not inside.any() or k[inside].max() > 0.0)
+        # strictly positive on the open support (Sec. II-B: the bump vanishes only at its ends)
+        assert np.all(k[inside] > 0.0)
         Lj = O.band_limit(lam, j, L)
         assert np.all(k[Lj:] == 0.0)
         pk = lam ** j
