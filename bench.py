@@ -437,10 +437,15 @@ def main():
         e2e = {"value": whole_job_rate(world, B, 1, 1000.0 * t_e2e), "unit": "maps/s", "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb}
 
-    # plain FP64 GPU path on a sample of maps, for the mixed/FP64 speedup
+    # plain FP64 GPU path on a sample of maps: the mixed/FP64 speedup, and the per-scale error
+    # of the mixed coefficients against the FP64 path's on the same map (the FP64 path matches
+    # the FP64 oracle to 1e-10 per scale at this size: tests/test_gpu_fullsize.py)
     fp64 = None
     if args.mode == "mixed" and args.fp64_sample_maps > 0 and rank == 0:
-        del W
+        with torch.cuda.stream(stream):
+            crv.crv_analysis(plan.handle, maps[0:1], W, Wphi, 1, stream.cuda_stream)  # mixed W of map 0
+        torch.cuda.synchronize()
+        plan.close()
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
             p64 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL | unrot_flag, max_batch=1, stream=stream.cuda_stream)
@@ -458,10 +463,20 @@ def main():
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b_) / n64
         rec64 = float(torch.linalg.vector_norm(o64[0] - maps[n64 - 1]) / torch.linalg.vector_norm(maps[n64 - 1]))
+        if n64 > 1:
+            with torch.cuda.stream(stream):
+                crv.crv_analysis(p64.handle, maps[0:1], W64, P64, 1, stream.cuda_stream)
+            torch.cuda.synchronize()
+        per_scale = {}
+        for j in range(J0, plan.J + 1):
+            ref = W64[j]
+            per_scale[str(j)] = float(torch.linalg.vector_norm(W[j].double() - ref) / torch.linalg.vector_norm(ref))
         fp64 = {"maps_per_s": 1000.0 / ms64, "ms_per_map": ms64, "sample_maps": n64,
                 "speedup_mixed_over_fp64": (1000.0 / ms64 and value / world / (1000.0 / ms64)),
-                "roundtrip_rel_l2": rec64}
+                "roundtrip_rel_l2": rec64, "mixed_vs_fp64_rel_l2_per_scale": per_scale,
+                "mixed_vs_fp64_rel_l2_max": max(per_scale.values())}
         p64.close()
+        del W64, P64
 
     # roofline of the dominant kernel kind
     peaks = measured_peaks()
@@ -502,13 +517,39 @@ def main():
                     "hbm_gbs_algorithmic": bytes_launch / (avg_ms * 1e-3) / 1e9}
         roof["avg_launch_ms"] = avg_ms
         roof["launches"] = kind_n[dom]
+        roof["launches_per_map"] = per_launch_units
+    # whole-map roofline: per kernel kind the larger of its algorithmic flops over its pipe's
+    # peak and its algorithmic bytes over HBM, summed over the kinds, against the measured time
+    # per map
+    roof_map = None
+    if kind_ms:
+        sm = clk.get("sm_mhz")
+        hbm = peaks["hbm_gbs"] * 1e9
+        t_roof = 0.0
+        parts = {}
+        for k, (bts, fl) in work.items():
+            if k not in kind_ms:
+                continue
+            if k.startswith("tc_"):
+                pk = peaks["bf16_tflops_sustained"] / 2.0 * 1e12
+            elif args.mode == "mixed":
+                pk = fp32_alu_peak_tflops(sm) * 1e12
+            else:
+                pk = fp64_alu_peak_tflops(sm) * 1e12
+            t = max(fl / pk, bts / hbm) * 1e3
+            parts[k] = t
+            t_roof += t
+        t_meas = ms_per_step / B
+        roof_map = {"t_roof_ms": t_roof, "t_measured_ms": t_meas, "frac": t_roof / t_meas, "per_kind_roof_ms": parts,
+                    "rule": "sum over kernel kinds of max(algorithmic flops / pipe peak, algorithmic bytes / HBM)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
         "config": config_dict(args), "p50_ms": p50, "p99_ms": p99, "latency_unit": "ms per map (analysis+synthesis)",
-        "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "e2e": e2e,
+        "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_map": roof_map,
+        "e2e": e2e,
         "fp64_path": fp64, "step_ms": step_ms,
         "kernels_ms_per_step": {k: v / args.steps for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
     }
@@ -523,7 +564,8 @@ def main():
             sys.stderr.write(f"{k:20s} {v / args.steps:10.2f} ms/step  {kind_n[k] // args.steps:7d} launches/step\n")
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
+    if plan.handle is not None:
+        plan.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -115,6 +115,13 @@ int crv_plan_info(crv_plan_t plan, int* J, int* Lj, size_t* w_elems, int* L_phi,
  * invalid). Clears the condition. */
 int crv_plan_check(crv_plan_t plan);
 
+/* As crv_plan_check, but ordered on one stream instead of the whole device: waits for the
+ * work already queued on `stream` (the stream the plan's calls ran on), then reads and clears
+ * the plan's error flag. Work of other streams and plans is not waited for, so a caller that
+ * runs several plans concurrently (one stream each) can collect one without stalling the
+ * others. CRV_ETIMEOUT as crv_plan_check; CRV_ECUDA if the stream reports an error. */
+int crv_plan_check_stream(crv_plan_t plan, void* stream);
+
 /* Self-test of that error path: launch, on the stream, one thread that waits on a device
  * barrier nothing arrives at, giving up after `polls` polls (1 <= polls <= 1e6) as every
  * bounded wait of the library does; the next crv_plan_check then returns CRV_ETIMEOUT.

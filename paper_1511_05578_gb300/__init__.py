@@ -15,7 +15,7 @@ import os
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CrvError",
-    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_check", "crv_debug_bounded_wait", "crv_plan_kernel",
+    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
     "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
     "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
@@ -56,6 +56,7 @@ def load():
         "crv_plan_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i),
                               ctypes.POINTER(sz)]),
         "crv_plan_check": (i, [vp]),
+        "crv_plan_check_stream": (i, [vp, vp]),
         "crv_debug_bounded_wait": (i, [vp, ctypes.c_long, vp]),
         "crv_plan_kernel": (i, [vp, i, ctypes.POINTER(d)]),
         "crv_plan_scaling": (i, [vp, ctypes.POINTER(d)]),
@@ -179,6 +180,12 @@ def crv_plan_info(plan):
 def crv_plan_check(plan):
     """Synchronise and raise CrvError(CRV_ETIMEOUT) if a bounded device wait gave up."""
     _check(load().crv_plan_check(plan))
+
+
+def crv_plan_check_stream(plan, stream=None):
+    """Wait for the work queued on `stream` only, then raise CrvError(CRV_ETIMEOUT) if a
+    bounded device wait of this plan gave up (no device-wide synchronisation)."""
+    _check(load().crv_plan_check_stream(plan, _stream(stream)))
 
 
 def crv_debug_bounded_wait(plan, polls, stream=None):

@@ -76,7 +76,7 @@ __host__ __device__ __forceinline__ double parity_sign(int k) { return (k & 1) ?
 // Kernel kinds, for launch accounting and optional event timing.
 enum KernelKind {
   K_DELTA = 0, K_SHT_CONTRACT, K_SHT_ROWS, K_BETA_SYNTH, K_BETA_QUAD, K_RING_INV_N, K_RING_INV_M,
-  K_RING_FWD_G, K_RING_FWD_A, K_CONTRACT_A, K_CONTRACT_S, K_TC_A, K_TC_S, K_MISC, K_NKINDS
+  K_RING_FWD_G, K_RING_FWD_A, K_CONTRACT_A, K_CONTRACT_S, K_TC_A, K_TC_S, K_MISC, K_SHT_BETA, K_NKINDS
 };
 const char* kind_name(int k);
 
@@ -92,6 +92,10 @@ struct KTimer {
 
 // Record a launch of one of our kernels (host side).
 void count_launch();
+// Per-device launch facts, cached per device ordinal (thread-safe): the current device's
+// SM count, and a kernel's dynamic shared-memory limit raised once on each device.
+int device_sms();
+bool func_attr_once(const void* kernel, int smem_bytes);
 // Check the last launch; on failure store a message and return false.
 bool launch_ok(const char* what);
 

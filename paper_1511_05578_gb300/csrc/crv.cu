@@ -28,7 +28,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static const char* kKindNames[K_NKINDS] = {"delta", "sht_contract", "sht_rows", "beta_synth", "beta_quad",
                                            "ring_inv_n", "ring_inv_m", "ring_fwd_g", "ring_fwd_a",
                                            "contract_analysis", "contract_synthesis", "tc_analysis",
-                                           "tc_synthesis", "misc"};
+                                           "tc_synthesis", "misc", "sht_beta"};
 const char* kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
 struct ProfState {
   std::mutex mu;
@@ -376,31 +376,45 @@ static int build_fft(crv_plan_s* p, int Lb) {
 // Launch helpers
 // ---------------------------------------------------------------------------
 
-template <class K>
-static bool set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return true;
-  static std::map<const void*, size_t> done;
-  static std::mutex mu;
-  std::lock_guard<std::mutex> g(mu);
-  auto it = done.find((const void*)kernel);
+// Function attributes and device properties are per device: both caches are keyed by the
+// device ordinal current at the call.
+namespace crv {
+static std::mutex g_dev_mu;
+bool func_attr_once(const void* kernel, int bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::map<std::pair<const void*, int>, int> done;
+  std::lock_guard<std::mutex> g(g_dev_mu);
+  auto it = done.find({kernel, dev});
   if (it != done.end() && it->second >= bytes) return true;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
     g_err = "cudaFuncSetAttribute(max dynamic smem) failed";
     return false;
   }
-  done[(const void*)kernel] = bytes;
+  done[{kernel, dev}] = bytes;
   return true;
 }
-
-static int num_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
-  }
+int device_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::map<int, int> sms;
+  std::lock_guard<std::mutex> g(g_dev_mu);
+  auto it = sms.find(dev);
+  if (it != sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  sms[dev] = n;
   return n;
 }
+}  // namespace crv
+
+template <class K>
+static bool set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return true;
+  return func_attr_once((const void*)kernel, (int)bytes);
+}
+
+static int num_sms() { return device_sms(); }
 
 // Persistent FFT blocks (one or two per SM, by shared memory and registers), each
 // looping over groups of G sequences.
@@ -467,7 +481,7 @@ static bool run_beta_synth(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* 
 
 template <class T, int NT, int PT>
 static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y,
-                             ColSet cs, T scale, int pa, int pb, int pc, PairMap pm, cudaStream_t s) {
+                             ColSet cs, T scale, int pa, int pb, int pc, PairMap pm, int kind, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
   const size_t smem = fft_smem_bytes<T>(NT);
@@ -476,22 +490,22 @@ static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, 
   const int npair = pm.idx ? pm.n : num_col_pairs(cs);
   if (npair <= 0) return true;
   const int grid = std::max(1, std::min((npair + G - 1) / G, num_sms() * bps));
-  KTimer kt(K_BETA_QUAD, s);
+  KTimer kt(kind, s);
   beta_quad_kernel<T, NT, PT><<<grid, NT, smem, s>>>(tb, ct, ncols, Lb, Xb, Y, cs, scale, pa, pb, pc, pm);
   kt.done();
   return launch_ok("beta_quad_kernel");
 }
 template <class T>
 static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, cx<T>* Y, ColSet cs, T scale,
-                          int pa, int pb, int pc, cudaStream_t s, PairMap pm = PairMap()) {
+                          int pa, int pb, int pc, cudaStream_t s, PairMap pm = PairMap(), int kind = K_BETA_QUAD) {
   const DftTab<T>& tb = dft_of<T>(fs);
   const CorrTab<T>& ct = corr_of<T>(fs);
   if (ct.Q != tb.P) { g_err = "beta quadrature needs Q == P"; return false; }
   if (ncols <= 0) return true;
   constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
-  return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, s);
+  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
+  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
+  return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +519,8 @@ static bool sht_forward(crv_plan_s* p, const double* map, cx<double>* flm, int L
   StSHTRow<double> sr{p->wF, Mc, m0, N, 1.0 / N};
   if (!run_rows<double>(K_SHT_ROWS, fs.d, -1, Ls, ld, sr, st)) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
-  if (!run_beta_quad<double>(fs, Ls, Mc, p->wF, p->wG, cs, 2 * M_PI, 1, 0, imod(3 * s, 4), st)) return false;
+  if (!run_beta_quad<double>(fs, Ls, Mc, p->wF, p->wG, cs, 2 * M_PI, 1, 0, imod(3 * s, 4), st, PairMap(), K_SHT_BETA))
+    return false;
   cudaMemsetAsync(flm, 0, sizeof(cx<double>) * Ls * Ls, st);
   dim3 g((Mc + 127) / 128, Ls);
   {
@@ -530,7 +545,7 @@ static bool sht_inverse(crv_plan_s* p, const cx<double>* flm, double* map, int L
   kt.done();
   if (!launch_ok("sht_inv_contract_kernel")) return false;
   ColSet cs{Mc, m0, 1, 0, 1, s};
-  if (!run_beta_synth<double>(fs.d, Ls, Mc, p->wG, p->wF, cs, K_BETA_SYNTH, st)) return false;
+  if (!run_beta_synth<double>(fs.d, Ls, Mc, p->wG, p->wF, cs, K_SHT_BETA, st)) return false;
   LdSHTRow<double> lr{p->wF, Mc, m0, N, real};
   StMapRow sm{map, N, real};
   return run_rows<double>(K_SHT_ROWS, fs.d, +1, Ls, lr, sm, st);
@@ -1080,6 +1095,21 @@ int crv_plan_check(crv_plan_t p) {
   cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (h) {
     cudaMemset(p->d_err, 0, sizeof(int));
+    return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
+  }
+  return CRV_OK;
+}
+
+int crv_plan_check_stream(crv_plan_t p, void* stream) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
+  if (h) {
+    cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
+    cudaStreamSynchronize(st);
     return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
   }
   return CRV_OK;

@@ -357,15 +357,7 @@ static bool use_ws() {
   }
   return v == 1;
 }
-static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
-  }
-  return n;
-}
+static int sm_count() { return device_sms(); }
 
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
                  int* err, int* ctr, cudaStream_t st, TcATab ta) {

@@ -110,6 +110,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
+// Wait (bounded) until every MMA this thread has issued is complete: one more commit to a
+// fresh mbarrier, which tcgen05.commit arms for all prior asynchronous tcgen05 operations of
+// the thread. Run by the issuing thread on every exit path, so that TMEM is never
+// deallocated under MMAs still in flight (a wait elsewhere may have given up mid-tile).
+__device__ __forceinline__ void mma_drain(uint64_t* bar, int* err) {
+  mma_commit(bar);
+  mbar_wait(bar, 0u, err);
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -168,7 +176,8 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   constexpr bool BULK = BulkB<Prob>::value;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // MMAs of the stage done
   uint64_t* full = bars + STAGES;                                             // B copies of the stage landed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + STAGES);
+  uint64_t* drain = full + STAGES;                                            // all MMAs of the CTA done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
 
   int mp, r0, c0g, kb, ke;
@@ -180,6 +189,7 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       mbar_init(&bars[s]);
       mbar_init(&full[s]);
     }
+    mbar_init(drain);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -291,6 +301,7 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       for (int s = 0; s < STAGES; ++s)
         if (pend & (1u << s)) mbar_wait(&full[s], (uint32_t)(pend_c[s] / STAGES) & 1u, err);
   }
+  if (tid == 0 && nchunks > 0) mma_drain(drain, err);
   fence_after();
   // Epilogue on all warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (the lanes it may
   // access) and the w / 4-th quarter of the BN columns.
@@ -376,7 +387,8 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* tr_full = acc_empty + 2;
   uint64_t* tr_empty = tr_full + D;
-  int* tring = reinterpret_cast<int*>(tr_empty + D);
+  uint64_t* drain = tr_empty + D;  // the MMA issuer's MMAs all done (every exit path)
+  int* tring = reinterpret_cast<int*>(drain + 1);
   int* abort_flag = tring + D;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(abort_flag + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -395,6 +407,7 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
       mbar_init(&tr_full[i], 1);
       mbar_init(&tr_empty[i], 6);  // B producer, MMA issuer, four epilogue warps
     }
+    mbar_init(drain);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -522,7 +535,7 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
     // ---- MMA issuer ----
     if (lane == 0) {
       uint32_t u = 0;
-      bool ok = true;
+      bool ok = true, issued = false;
       for (uint32_t j = 0; ok; ++j) {
         const int sl = j % D;
         if (!mbar_wait(&tr_full[sl], (j / D) & 1u, err)) break;
@@ -552,12 +565,14 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
             mma_tf32(acc, ahi, blo, G::IDESC, 1u);
             mma_tf32(acc, ahi, bhi, G::IDESC, 1u);
           }
+          issued = true;
           mma_commit(&empty[s]);
         }
         if (!ok) break;
         if (nch > 0) mma_commit(&acc_full[a]);
         else mbar_arrive(&acc_full[a]);
       }
+      if (issued) mma_drain(drain, err);
     }
   } else {
     // ---- epilogue: warp w may read TMEM lanes 32 (w % 4) .. + 31 ----
@@ -608,13 +623,7 @@ __global__ void bounded_wait_probe_kernel(int* err, long limit) {
 
 template <class Prob, int BN>
 bool launch_tc_gemm(const Prob& pb, dim3 grid, int* err, cudaStream_t st, int kind) {
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(tc::tc_gemm_kernel<Prob, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::Geo<BN>::SMEM_BYTES) != cudaSuccess)
-      return false;
-    attr = true;
-  }
+  if (!func_attr_once((const void*)tc::tc_gemm_kernel<Prob, BN>, tc::Geo<BN>::SMEM_BYTES)) return false;
   KTimer kt(kind, st);
   tc::tc_gemm_kernel<Prob, BN><<<grid, tc::NT, tc::Geo<BN>::SMEM_BYTES, st>>>(pb, err);
   kt.done();
@@ -625,13 +634,7 @@ bool launch_tc_gemm(const Prob& pb, dim3 grid, int* err, cudaStream_t st, int ki
 // ctr: a device int, zeroed here on the stream before the launch.
 template <class Prob, int BN>
 bool launch_tc_gemm_ws(const Prob& pb, dim3 grid, int nsm, int* ctr, int* err, cudaStream_t st, int kind) {
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(tc::tc_gemm_ws_kernel<Prob, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::GeoWS<BN>::SMEM_BYTES) != cudaSuccess)
-      return false;
-    attr = true;
-  }
+  if (!func_attr_once((const void*)tc::tc_gemm_ws_kernel<Prob, BN>, tc::GeoWS<BN>::SMEM_BYTES)) return false;
   const long long nt = (long long)grid.x * grid.y * grid.z;
   if (nt <= 0) return true;
   if (nt > 0x7fffffffLL) return false;

@@ -316,14 +316,16 @@ class CudaExecutor:
             ev = torch.cuda.Event()
             ev.record(s)
         keep += [dmaps, W, Wphi, dout]
-        return {"ev": ev, "out": out_host, "keep": keep, "plan": plan, "inputs": dmaps}
+        return {"ev": ev, "out": out_host, "keep": keep, "plan": plan, "inputs": dmaps, "stream": s}
 
     def done(self, h):
         return h["ev"].query()
 
     def finish(self, h):
-        """Reconstructed maps (host), after checking the plan's device-side error flag."""
-        self.crv.crv_plan_check(h["plan"].handle)
+        """Reconstructed maps (host), after checking the plan's device-side error flag on the
+        request's own stream (already complete: no wait, and no device-wide synchronisation
+        that would stall the other running requests)."""
+        self.crv.crv_plan_check_stream(h["plan"].handle, h["stream"])
         out = h["out"].numpy().copy()
         h.clear()
         return out

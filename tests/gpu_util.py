@@ -12,6 +12,14 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
+def max_rel(a, b):
+    """Element-wise error scaled by the reference's largest entry: max|a - b| / max|b|.
+    One wrong entry shows here at its own size, where a norm over a whole scale would
+    dilute it."""
+    mb = np.abs(b).max() if np.size(b) else 0.0
+    return np.abs(a - b).max() / (mb if mb > 0 else 1.0) if np.size(b) else 0.0
+
+
 def map_to_device(fmap, real):
     import torch
     a = np.asarray(fmap)

@@ -41,3 +41,22 @@ def test_bounded_wait_gives_up_and_reports_then_plan_still_works():
     crv.crv_plan_check(p.handle)
     assert rel_l2(map_from_device(out, True), fmap) < 1e-5
     p.close()
+
+
+def test_stream_ordered_check_reports_and_leaves_other_streams_alone():
+    """crv_plan_check_stream reads the error flag in the order of one stream: a probe that
+    gives up on stream s1 is reported by the check on s1, once; a check of a second plan on
+    its own stream s2 is clean meanwhile."""
+    L, lam, J0 = 32, 2.0, 2
+    p1 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL | crv.CRV_F_MIXED)
+    p2 = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL | crv.CRV_F_MIXED)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    crv.crv_plan_check(p1.handle)
+    crv.crv_debug_bounded_wait(p1.handle, 2000, s1)
+    crv.crv_plan_check_stream(p2.handle, s2)  # the other plan's flag is clean
+    with pytest.raises(crv.CrvError) as e:
+        crv.crv_plan_check_stream(p1.handle, s1)
+    assert e.value.status == crv.CRV_ETIMEOUT
+    crv.crv_plan_check_stream(p1.handle, s1)  # cleared
+    p1.close()
+    p2.close()

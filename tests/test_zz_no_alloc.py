@@ -55,6 +55,24 @@ def test_noalloc_delta_matches_plan_twice():
     p2.close()
 
 
+def test_noalloc_delta_at_its_size_limit_matches_oracle():
+    """At the scratch array's limit (L = CRV_NOALLOC_MAX_L) a few rows of the table, including
+    the last one, against the oracle's Delta, which Risbo's recursion computes independently of
+    the library's (the same bar as the plan's Delta tests)."""
+    import oracle as O
+    import paper_1511_05578_gb300 as crv
+    L = crv.CRV_NOALLOC_MAX_L
+    Q = torch.full((L ** 3,), float("nan"), dtype=torch.float64, device="cuda")
+    crv.crv_delta_table_noalloc(L, Q)
+    torch.cuda.synchronize()
+    Qh = Q.view(L, L, L)
+    for l in (0, 1, L // 2 - 1, L - 1):
+        got = Qh[: l + 1, l, : l + 1].cpu().numpy()
+        want = O.delta_matrix(l)[l:, l:]         # m', n >= 0 quadrant
+        assert np.abs(got - want).max() < 1e-14 + 2e-16 * l, l
+    del Q
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import paper_1511_05578_gb300 as crv
     Q = torch.zeros(8, dtype=torch.float64, device="cuda")
