@@ -313,7 +313,7 @@ static int build_fft(crv_plan_s* p, int Lb) {
     for (int e = 0; e < 4; ++e)
       for (int k = 0; k < Ns; ++k) stw.push_back(std::polar(1.0, -2 * M_PI * (double)k * (1 << e) / (16.0 * Ns)));
   if (stw.empty()) stw.push_back(1.0);
-  std::vector<std::complex<double>> chirp(N), kf(P, 0.0), ki(P, 0.0), wv(Q, 0.0), hp(N);
+  std::vector<std::complex<double>> chirp(N), kf(P, 0.0), ki(P, 0.0), wv(Q, 0.0), hp(N), bsyn(N), bquad(N);
   for (int j = 0; j < N; ++j) {  // e^{i pi m/N} with m = j or j - N (|m| < Lb)
     const int m = (j < Lb) ? j : j - N;
     hp[j] = std::polar(1.0, M_PI * (double)m / N);
@@ -321,6 +321,10 @@ static int build_fft(crv_plan_s* p, int Lb) {
   for (int t = 0; t < N; ++t) {
     long long r = ((long long)t * t) % (2LL * N);
     chirp[t] = std::polar(1.0, -M_PI * (double)r / N);
+  }
+  for (int j = 0; j < N; ++j) {
+    bsyn[j] = hp[j] * std::conj(chirp[j]);
+    bquad[j] = chirp[j] * std::conj(hp[j]) / (double)N;
   }
   for (int t = -(N - 1); t <= N - 1; ++t) {
     const int a = t < 0 ? -t : t;
@@ -365,6 +369,8 @@ static int build_fft(crv_plan_s* p, int Lb) {
   up(kf, d, f); s.d.khat_f = d; s.f.khat_f = f;
   up(ki, d, f); s.d.khat_i = d; s.f.khat_i = f;
   up(hp, d, f); s.d.hphase = d; s.f.hphase = f;
+  up(bsyn, d, f); s.d.bsyn = d; s.f.bsyn = f;
+  up(bquad, d, f); s.d.bquad = d; s.f.bquad = f;
   s.cd.Q = s.cf.Q = Q;
   up(wv, d, f); s.cd.what = d; s.cf.what = f;
   if (st != CRV_OK) return st;

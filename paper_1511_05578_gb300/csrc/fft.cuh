@@ -33,6 +33,8 @@ struct DftTab {
   const cx<T>* khat_f = nullptr;  // [P]  FFT_P(conj h wrapped) / P   (forward DFT, sign -1)
   const cx<T>* khat_i = nullptr;  // [P]  FFT_P(h wrapped) / P        (inverse DFT, sign +1)
   const cx<T>* hphase = nullptr;  // [N]  e^{+i pi m/N}, m = j (j < (N+1)/2) or j - N: half-sample phase of beta_b
+  const cx<T>* bsyn = nullptr;    // [N]  hphase[j] conj(h_j): the beta synthesis's two input factors in one
+  const cx<T>* bquad = nullptr;   // [N]  h_k conj(hphase[k]) / N: the beta quadrature's two output factors in one
 };
 
 // Weight spectrum for the correlation of Eq. gmnmp (same P as the DftTab of the length).

@@ -351,6 +351,8 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
 // ---------------------------------------------------------------------------
 constexpr int WS_STAGES = 4, WS_TRING = 4;
 template <class Prob> struct WsWarps { static constexpr int value = BulkA<Prob>::value ? 1 : 16; };  // producer warps
+// K chunks of A whose loads a producer thread keeps in flight ahead of the one it stores
+template <class Prob> struct WsPrefetch { static constexpr int value = 4; };
 template <int BN> struct GeoWS {
   static constexpr int SMEM_BYTES = WS_STAGES * Geo<BN>::STAGE_BYTES + 1024 + 512;
   static constexpr uint32_t TMEM_COLS = 2 * Geo<BN>::TMEM_COLS;
@@ -460,18 +462,19 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
       int mp, r0, c0, kb, nch;
       tile_of(t, mp, r0, c0, kb, nch);
       if (BA) nch = 0;  // A arrives with B
-      float x0[NQ][4], x1[NQ][4];
+      // the loads of the next PD chunks are in flight while a chunk is split and stored
+      constexpr int PD = WsPrefetch<Prob>::value;
+      float xs[PD][NQ][4];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        if (nch > 0) pb.a4(mp, r0, kb, pr, pq + q * PQ, x0[q]);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q)
-        if (nch > 1) pb.a4(mp, r0, kb + BK, pr, pq + q * PQ, x1[q]);
-      for (int c = 0; c < nch; ++c, ++u) {
-        float x2[NQ][4];
+      for (int d = 0; d < PD; ++d)
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
-          if (c + 2 < nch) pb.a4(mp, r0, kb + (c + 2) * BK, pr, pq + q * PQ, x2[q]);
+          if (nch > d) pb.a4(mp, r0, kb + d * BK, pr, pq + q * PQ, xs[d][q]);
+      for (int c = 0; c < nch; ++c, ++u) {
+        float xn[NQ][4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if (c + PD < nch) pb.a4(mp, r0, kb + (c + PD) * BK, pr, pq + q * PQ, xn[q]);
         const int s = u % S;
         if (!warp_wait(&empty[s], ((u / S) + 1) & 1u, err)) {
           *abort_flag = 1;
@@ -479,14 +482,20 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
         }
         unsigned char* st = base + s * STAGE_BYTES;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) put4(st, st + A_BYTES, pr, pq + q * PQ, x0[q]);
+        for (int q = 0; q < NQ; ++q) put4(st, st + A_BYTES, pr, pq + q * PQ, xs[0][q]);
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&a_full[s]);
 #pragma unroll
+        for (int d = 0; d + 1 < PD; ++d)
+#pragma unroll
+          for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xs[d][q][i] = xs[d + 1][q][i];
+#pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) { x0[q][i] = x1[q][i]; x1[q][i] = x2[q][i]; }
+          for (int i = 0; i < 4; ++i) xs[PD - 1][q][i] = xn[q][i];
       }
       __syncwarp();
       producers_sync<PW>();  // a failure in any warp (abort_flag) ends the loop at the next tile

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_k
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = t + q * TP;
-      if (j < N) v[q] = v[q] * tb.hphase[j] * chirp_of(tb, j, +1);
+      if (j < N) v[q] = v[q] * tb.bsyn[j];
     }
     fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
@@ -586,16 +586,18 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
-  const T invN = (T)1 / (T)N;
   const int span = (npair + gridDim.x * G - 1) / (gridDim.x * G) * G;
   const int s_end = min(npair, (blockIdx.x + 1) * span);
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
     const int p = s0 + g;
     const bool valid = p < s_end;
-    const ColPair cp = valid ? col_pair(cs, pm.idx ? pm.idx[p] : p) : ColPair{0, -1, 0};
-    // extensions to the 2Lb-1 nodes of the full circle, summed, then the chirp
     cx<T> v[16];
-    load_pair_ext<T>(v, Xb, ncols, cp, valid, Lb, N, t, TP, 1, buf);
+    {
+      // extensions to the 2Lb-1 nodes of the full circle, summed, then the chirp (the pair's
+      // descriptor is rebuilt for the unfold below rather than kept live across the FFTs)
+      const ColPair cp = valid ? col_pair(cs, pm.idx ? pm.idx[p] : p) : ColPair{0, -1, 0};
+      load_pair_ext<T>(v, Xb, ncols, cp, valid, Lb, N, t, TP, 1, buf);
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = t + q * TP;
@@ -611,7 +613,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int k = t + q * TP;
-        if (q < 8 && k < N) x[k < Lb ? k : k - N + Q] = v[q] * chirp_of(tb, k, -1) * (conj(tb.hphase[k]) * invN);
+        if (q < 8 && k < N) x[k < Lb ? k : k - N + Q] = v[q] * tb.bquad[k];
         if (k >= Lb && k <= Q - Lb) x[k] = mk<T>(0, 0);
       }
       __syncthreads();
@@ -631,6 +633,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     }
     __syncthreads();
     if (valid) {
+      const ColPair cp = col_pair(cs, pm.idx ? pm.idx[p] : p);
       const int phA = imod(cp.mA * pa + cp.n * pb + pc, 4), phB = imod((cp.mA + 1) * pa + cp.n * pb + pc, 4);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
