@@ -18,11 +18,11 @@ __all__ = [
     "risbo_matrix", "delta_matrix", "quad_weight", "sht_inverse", "sht_forward",
     "s_lambda", "k_lambda", "J_max", "band_limit", "L_phi", "kappa", "phi_scaling", "zeta", "zeta_unrotated", "psi",
     "euler_matrix", "euler_angles", "analysis_point", "analysis_rings", "analysis_from_flm", "analysis", "scaling_map", "wigner_forward_Y",
-    "wigner_forward_coeffs", "synthesis_flm", "synthesis", "MUTATION",
+    "wigner_forward_coeffs", "synthesis_flm", "synthesis", "rotate_wigner", "rotate_wigner_adjoint", "MUTATION",
 ]
 
 # Deliberate-mistake switches, used only by tests that check the pins catch them.
-MUTATION = {"ext_sign": False, "half_phase": False, "weight_sign": False}
+MUTATION = {"ext_sign": False, "half_phase": False, "weight_sign": False, "rotation_transposed": False}
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -441,3 +441,53 @@ def synthesis_flm(W, Wphi, lam, J0, s, L, scales=None, unrotated=False):
 def synthesis(W, Wphi, lam, J0, s, L, unrotated=False):
     """Curvelet synthesis back to the MW map (complex [L][2L-1])."""
     return sht_inverse(synthesis_flm(W, Wphi, lam, J0, s, L, unrotated=unrotated), L, s)
+
+
+# --------------------------------------------------------------------------
+# Rotation of Wigner coefficients (Sec. III-A-1, Eqs. curvelet_Wigner,
+# curvelet_Wigner_inverse and rotateWigner)
+# --------------------------------------------------------------------------
+def _edge_d(l, th):
+    """Columns n = +l and n = -l of d^l(vartheta) as arrays over k = -l..l (Risbo)."""
+    d = risbo_matrix(l, th)
+    if MUTATION["rotation_transposed"]:
+        d = d.T
+    return d[:, 2 * l], d[:, 0]
+
+
+def rotate_wigner(wt, lam, j, s, Lj):
+    """Wigner coefficients of the rotated curvelet coefficients from those of the unrotated
+    ones. W(rho) = W~(rho rho*) with rho* = (0, vartheta^j, 0) (Eq. rotateWigner) and
+    D^l(rho rho*) = D^l(rho) D^l(rho*) give (W)^l_mk = sum_n (W~)^l_mn d^l_kn(vartheta^j),
+    and (W~)^l_mn vanishes unless |n| = l (Eq. curvelet_Wigner_property), so two terms:
+        (W)^l_mk = (W~)^l_{m,l} d^l_{k,l}(vartheta) + (W~)^l_{m,-l} d^l_{k,-l}(vartheta).
+    wt: [2][Lj][2Lj-1] complex, wt[0][l][m + Lj - 1] = (W~)^l_{m,l}, wt[1][...] = (W~)^l_{m,-l}
+    (wt[1][0] unused: at l = 0 the two coincide). Returns dense [Lj][2Lj-1][2Lj-1] (m, k)."""
+    N = 2 * Lj - 1
+    th = math.acos(-s / lam ** j)
+    out = np.zeros((Lj, N, N), dtype=np.complex128)
+    for l in range(Lj):
+        dp, dm = _edge_d(l, th)
+        ms = slice(Lj - 1 - l, Lj + l)
+        a = wt[0][l, ms]
+        out[l, ms, ms] = a[:, None] * dp[None, :]
+        if l > 0:
+            out[l, ms, ms] += wt[1][l, ms][:, None] * dm[None, :]
+    return out
+
+
+def rotate_wigner_adjoint(w, lam, j, s, Lj):
+    """Adjoint of rotate_wigner: (W~)^l_{m,+-l} = sum_k (W)^l_mk d^l_{k,+-l}(vartheta^j); the
+    inverse on coefficients of the form rotate_wigner(wt) (d^l is orthogonal). Returns
+    [2][Lj][2Lj-1] as rotate_wigner takes it (wt[1][0] = 0)."""
+    N = 2 * Lj - 1
+    th = math.acos(-s / lam ** j)
+    wt = np.zeros((2, Lj, N), dtype=np.complex128)
+    for l in range(Lj):
+        dp, dm = _edge_d(l, th)
+        ms = slice(Lj - 1 - l, Lj + l)
+        blk = w[l, ms, ms]
+        wt[0][l, ms] = blk @ dp
+        if l > 0:
+            wt[1][l, ms] = blk @ dm
+    return wt
