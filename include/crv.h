@@ -97,15 +97,29 @@ enum {
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule,
                     unsigned flags, int max_batch, void* stream);
 
-/* Free a plan and all its device memory (synchronises the device first). NULL is ok. */
+/* Free a plan and its device memory (synchronises the device first). NULL is ok. The
+ * read-only tables a plan shares with its clones are freed with the last of them. */
 int crv_plan_destroy(crv_plan_t plan);
+
+/* A second instance of a plan for concurrent use on another stream (a plan serves one stream
+ * at a time). The clone shares the source's read-only tables (Delta^l(pi/2), the tensor-core
+ * Delta Psi tables, FFT tables, kernels) by reference count and allocates only its own
+ * workspace (f_lm buffers, the (m, n, m') volumes, ring buffer, per-map tensor-core A tables,
+ * error flag), so concurrent requests of the same (L, lambda, J0, spin, flags) hold the tables
+ * once. The two plans are independent otherwise: either may be destroyed first. Synchronises
+ * the stream. CRV_ENOMEM if the workspace does not fit; on error *out is NULL. */
+int crv_plan_clone(crv_plan_t* out, crv_plan_t src, void* stream);
+
+/* Device bytes of a plan: table_bytes of its (shared) read-only tables, workspace_bytes of its
+ * own workspace. Either pointer may be NULL. A clone adds workspace_bytes to the device. */
+int crv_plan_bytes(crv_plan_t plan, size_t* table_bytes, size_t* workspace_bytes);
 
 /* Sizes of a plan. Any output pointer may be NULL.
  *   J                 largest scale
  *   Lj[j], j=0..J     band limit of scale j (entries j < J0 are 0)
  *   w_elems[j]        samples per map of W_j (L_j (2L_j-1)^2; 0 for j < J0)
  *   L_phi             band limit of the scaling map
- *   workspace_bytes   device memory the plan holds (tables + workspace)
+ *   workspace_bytes   device memory the plan uses (its shared tables + its own workspace)
  * Lj and w_elems must have room for J+1 entries (J <= 64). */
 int crv_plan_info(crv_plan_t plan, int* J, int* Lj, size_t* w_elems, int* L_phi,
                   size_t* workspace_bytes);
@@ -168,6 +182,29 @@ int crv_synthesis(crv_plan_t plan, const void* const* W, const void* Wphi, void*
 int crv_analysis_lm(crv_plan_t plan, const void* flm, void* const* W, void* Wphi, int B, void* stream);
 int crv_synthesis_lm(crv_plan_t plan, const void* const* W, const void* Wphi, void* flm, int B,
                      void* stream);
+
+/* Rotation of Wigner coefficients of scale j (Sec. III-A-1, Eqs. curvelet_Wigner,
+ * curvelet_Wigner_inverse, rotateWigner): from the Wigner coefficients of the unrotated
+ * curvelet coefficients W~_j (the paper's fast representation) to those of the rotated W_j.
+ * With rho* = (0, vartheta^j, 0), vartheta^j = arccos(-s/lambda^j), W(rho) = W~(rho rho*)
+ * gives (W)^l_mk = sum_n (W~)^l_mn d^l_kn(vartheta^j); (W~)^l_mn vanishes unless |n| = l
+ * (Eq. curvelet_Wigner_property), so
+ *     (W)^l_mk = (W~)^l_{m,l} d^l_{k,l}(vartheta^j) + (W~)^l_{m,-l} d^l_{k,-l}(vartheta^j),
+ * O(L_j^3) per scale. Coefficients are those of W(rho) = sum (2l+1)/(8pi^2) (W)^l_mn D^l*_mn(rho)
+ * with D^l_mn(a, b, g) = e^{-ima} d^l_mn(b) e^{-ing}; e.g. (W~)^l_mn = (8pi^2/(2l+1)) f_lm Psi~_ln.
+ *   j   scale, J0 <= j <= J (any plan: vartheta^j depends only on lambda, j and the spin)
+ *   wt  [B][2][L_j][2L_j-1] complex double: wt[b][0][l][m + L_j - 1] = (W~)^l_{m,l},
+ *       wt[b][1][l][m + L_j - 1] = (W~)^l_{m,-l} (entries |m| > l and wt[b][1][0] are ignored)
+ *   w   [B][L_j][2L_j-1][2L_j-1] complex double: w[b][l][m + L_j - 1][k + L_j - 1] = (W)^l_mk,
+ *       zero where |m| > l or |k| > l
+ * Device pointers, stream-ordered; CRV_EINVAL for j outside [J0, J], B outside [0, max_batch]
+ * or a NULL pointer with B > 0. FP64. */
+int crv_rotate_wigner(crv_plan_t plan, int j, const void* wt, void* w, int B, void* stream);
+
+/* Adjoint of crv_rotate_wigner: (W~)^l_{m,+-l} = sum_k (W)^l_mk d^l_{k,+-l}(vartheta^j), which
+ * inverts it on rotated coefficients (d^l is orthogonal); writes every entry of wt (zeros for
+ * |m| > l and for wt[b][1][0]). Same layouts and errors as crv_rotate_wigner. */
+int crv_rotate_wigner_adjoint(crv_plan_t plan, int j, const void* w, void* wt, int B, void* stream);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* crv_last_error(void);

@@ -15,9 +15,9 @@ import os
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CrvError",
-    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
+    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
-    "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
+    "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_rotate_wigner", "crv_rotate_wigner_adjoint", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
     "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
     "Plan",
 ]
@@ -53,6 +53,8 @@ def load():
     sig = {
         "crv_plan_create": (i, [ctypes.POINTER(vp), i, d, i, i, i, u, i, vp]),
         "crv_plan_destroy": (i, [vp]),
+        "crv_plan_clone": (i, [ctypes.POINTER(vp), vp, vp]),
+        "crv_plan_bytes": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
         "crv_plan_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i),
                               ctypes.POINTER(sz)]),
         "crv_plan_check": (i, [vp]),
@@ -67,6 +69,8 @@ def load():
         "crv_synthesis": (i, [vp, ctypes.POINTER(vp), vp, vp, i, vp]),
         "crv_analysis_lm": (i, [vp, vp, ctypes.POINTER(vp), vp, i, vp]),
         "crv_synthesis_lm": (i, [vp, ctypes.POINTER(vp), vp, vp, i, vp]),
+        "crv_rotate_wigner": (i, [vp, i, vp, vp, i, vp]),
+        "crv_rotate_wigner_adjoint": (i, [vp, i, vp, vp, i, vp]),
         "crv_last_error": (ctypes.c_char_p, []),
         "crv_status_string": (ctypes.c_char_p, [i]),
         "crv_launch_count": (ctypes.c_ulonglong, []),
@@ -164,6 +168,21 @@ def crv_plan_destroy(plan):
     _check(load().crv_plan_destroy(plan))
 
 
+def crv_plan_clone(plan, stream=None):
+    """A second instance sharing `plan`'s read-only tables, with its own workspace."""
+    h = load()
+    out = ctypes.c_void_p()
+    _check(h.crv_plan_clone(ctypes.byref(out), plan, _stream(stream)))
+    return out
+
+
+def crv_plan_bytes(plan):
+    """(table_bytes, workspace_bytes) of a plan: its shared tables and its own workspace."""
+    t, w = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().crv_plan_bytes(plan, ctypes.byref(t), ctypes.byref(w)))
+    return t.value, w.value
+
+
 def crv_plan_info(plan):
     h = load()
     J = ctypes.c_int()
@@ -242,16 +261,42 @@ def crv_synthesis_lm(plan, W, Wphi, flm, B, stream=None):
     _check(load().crv_synthesis_lm(plan, _ptr_array(W, len(W)), _ptr(Wphi), _ptr(flm), int(B), _stream(stream)))
 
 
+def crv_rotate_wigner(plan, j, wt, w, B, stream=None):
+    """Wigner coefficients of the rotated curvelet coefficients of scale j from those of the
+    unrotated ones (see include/crv.h): wt [B][2][L_j][2L_j-1], w [B][L_j][2L_j-1][2L_j-1],
+    complex128 device tensors."""
+    _check(load().crv_rotate_wigner(plan, int(j), _ptr(wt), _ptr(w), int(B), _stream(stream)))
+
+
+def crv_rotate_wigner_adjoint(plan, j, w, wt, B, stream=None):
+    _check(load().crv_rotate_wigner_adjoint(plan, int(j), _ptr(w), _ptr(wt), int(B), _stream(stream)))
+
+
 class Plan:
     """Owns a plan handle; allocates correctly shaped torch tensors for its data."""
 
-    def __init__(self, L, lam=2.0, J0=2, spin=0, flags=0, max_batch=1, stream=None):
+    def __init__(self, L, lam=2.0, J0=2, spin=0, flags=0, max_batch=1, stream=None, share=None):
+        """share: an existing Plan of the same parameters whose read-only tables this one
+        shares (crv_plan_clone); only a workspace is allocated."""
         self.L, self.lam, self.J0, self.spin, self.flags, self.max_batch = L, lam, J0, spin, flags, max_batch
-        self.handle = crv_plan_create(L, lam, J0, spin, CRV_NRULE_CURVELET, flags, max_batch, stream)
+        if share is not None:
+            self.handle = crv_plan_clone(share.handle, stream)
+        else:
+            self.handle = crv_plan_create(L, lam, J0, spin, CRV_NRULE_CURVELET, flags, max_batch, stream)
         info = crv_plan_info(self.handle)
         self.J, self.Lj, self.L_phi, self.bytes = info["J"], info["Lj"], info["L_phi"], info["workspace_bytes"]
         self.real = bool(flags & CRV_F_REAL)
         self.w_dtype_name = "float32" if flags & CRV_F_W_FP32 else "float64"
+
+    def clone(self, stream=None):
+        """A Plan sharing this one's tables, for concurrent use on another stream."""
+        return Plan(self.L, self.lam, self.J0, self.spin, self.flags, self.max_batch, stream, share=self)
+
+    def table_bytes(self):
+        return crv_plan_bytes(self.handle)[0]
+
+    def own_bytes(self):
+        return crv_plan_bytes(self.handle)[1]
 
     def close(self):
         if self.handle is not None:
@@ -292,6 +337,18 @@ class Plan:
             shape = (B, Lb, N, N) + (() if self.real else (2,))
             out.append(torch.zeros(shape, dtype=dt, device="cuda"))
         return out
+
+    def wigner_tensor(self, j, B=1):
+        """Dense Wigner coefficients of scale j: complex128 [B][L_j][2L_j-1][2L_j-1]."""
+        torch = self._t()
+        Lb = self.Lj[j]
+        return torch.zeros((B, Lb, 2 * Lb - 1, 2 * Lb - 1), dtype=torch.complex128, device="cuda")
+
+    def wigner_edge_tensor(self, j, B=1):
+        """Unrotated (|n| = l) Wigner coefficients of scale j: complex128 [B][2][L_j][2L_j-1]."""
+        torch = self._t()
+        Lb = self.Lj[j]
+        return torch.zeros((B, 2, Lb, 2 * Lb - 1), dtype=torch.complex128, device="cuda")
 
     def Wphi_tensor(self, B=1):
         return self.map_tensor(B, self.L_phi)

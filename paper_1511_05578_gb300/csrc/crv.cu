@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <atomic>
 #include <set>
@@ -15,6 +16,7 @@
 
 #include "../../include/crv.h"
 #include "contract.cuh"
+#include "rotate.cuh"
 #include "tc_contract.cuh"
 
 namespace crv {
@@ -28,7 +30,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static const char* kKindNames[K_NKINDS] = {"delta", "sht_contract", "sht_rows", "beta_synth", "beta_quad",
                                            "ring_inv_n", "ring_inv_m", "ring_fwd_g", "ring_fwd_a",
                                            "contract_analysis", "contract_synthesis", "tc_analysis",
-                                           "tc_synthesis", "misc", "sht_beta"};
+                                           "tc_synthesis", "misc", "sht_beta", "rotate"};
 const char* kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
 struct ProfState {
   std::mutex mu;
@@ -214,6 +216,20 @@ struct FftSet {
   CorrTab<double> cd; CorrTab<float> cf;
 };
 
+// Device allocations of the read-only tables of a plan (Delta, Delta Psi tensor-core
+// tables, FFT tables, kernels): one set per crv_plan_create, shared by the plan and its clones
+// (crv_plan_clone) and freed with the last of them.
+struct TableSet {
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  TableSet() = default;
+  TableSet(const TableSet&) = delete;
+  TableSet& operator=(const TableSet&) = delete;
+  ~TableSet() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
 struct crv_plan_s {
   int L = 0, J0 = 0, J = 0, spin = 0, max_batch = 0, Lphi = 1;
   unsigned flags = 0;
@@ -230,6 +246,7 @@ struct crv_plan_s {
   std::vector<double> kappa;  // [J+1][L]
   std::vector<double> phi;    // [L]
   std::vector<std::vector<double>> psi;  // per j: [Lj][2Lj-1]
+  std::vector<double*> dedge;            // per j: d^l_{k,l}(vartheta^j) at [l][k + Lj - 1] (rotation of Wigner coefficients)
   double* dQ = nullptr;
   float* dQ32 = nullptr;
   std::vector<double*> dpsi;
@@ -250,13 +267,13 @@ struct crv_plan_s {
   std::vector<TcATab> tabAA;        // per scale: chunk offsets of the per-map A tables (one buffer)
   int* d_err = nullptr;   // [0]: set by kernels whose bounded waits gave up; [1]: tile counter of the tensor-core engine
   size_t vol_bytes = 0, ring_bytes = 0;
-  std::vector<void*> allocs;
+  long long a_chunks = 0;  // chunks of the per-map A tables of the analysis (largest scale)
+  std::shared_ptr<TableSet> tabs;  // read-only tables, shared with clones
+  std::vector<void*> allocs;       // this instance's workspace
   size_t bytes = 0;
 
-  template <class P> P* dalloc(size_t n, int* status) {
-    if (*status != CRV_OK) return nullptr;
+  static void* raw_alloc(size_t b, int* status) {
     void* p = nullptr;
-    size_t b = n * sizeof(P);
     if (b == 0) b = 16;
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
@@ -264,8 +281,24 @@ struct crv_plan_s {
       *status = fail(CRV_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
       return nullptr;
     }
+    return p;
+  }
+  // workspace (per instance)
+  template <class P> P* dalloc(size_t n, int* status) {
+    if (*status != CRV_OK) return nullptr;
+    void* p = raw_alloc(n * sizeof(P), status);
+    if (!p) return nullptr;
     allocs.push_back(p);
-    bytes += b;
+    bytes += std::max<size_t>(n * sizeof(P), 16);
+    return (P*)p;
+  }
+  // read-only tables (shared)
+  template <class P> P* talloc(size_t n, int* status) {
+    if (*status != CRV_OK) return nullptr;
+    void* p = raw_alloc(n * sizeof(P), status);
+    if (!p) return nullptr;
+    tabs->allocs.push_back(p);
+    tabs->bytes += std::max<size_t>(n * sizeof(P), 16);
     return (P*)p;
   }
   ~crv_plan_s() {
@@ -349,8 +382,8 @@ static int build_fft(crv_plan_s* p, int Lb) {
   int st = CRV_OK;
   FftSet s;
   auto up = [&](const std::vector<std::complex<double>>& v, cx<double>*& dd, cx<float>*& df) {
-    dd = p->dalloc<cx<double>>(v.size(), &st);
-    df = p->dalloc<cx<float>>(v.size(), &st);
+    dd = p->talloc<cx<double>>(v.size(), &st);
+    df = p->talloc<cx<float>>(v.size(), &st);
     if (st != CRV_OK) return;
     std::vector<cx<double>> hd(v.size());
     std::vector<cx<float>> hf(v.size());
@@ -850,10 +883,10 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
         total += range[i].y;
       }
       const size_t nf = (size_t)std::max<long long>(total, 1) * TC_CHUNK_FLOATS;
-      float* hi = p->dalloc<float>(nf, &stt);
-      float* lo = p->dalloc<float>(nf, &stt);
-      long long* dbase = p->dalloc<long long>(base.size(), &stt);
-      int2* drange = p->dalloc<int2>(range.size(), &stt);
+      float* hi = p->talloc<float>(nf, &stt);
+      float* lo = p->talloc<float>(nf, &stt);
+      long long* dbase = p->talloc<long long>(base.size(), &stt);
+      int2* drange = p->talloc<int2>(range.size(), &stt);
       if (stt != CRV_OK) return stt;
       cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
       cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
@@ -880,8 +913,8 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
       total += range[i].y;
     }
     amax = std::max(amax, total);
-    long long* dbase = p->dalloc<long long>(base.size(), &stt);
-    int2* drange = p->dalloc<int2>(range.size(), &stt);
+    long long* dbase = p->talloc<long long>(base.size(), &stt);
+    int2* drange = p->talloc<int2>(range.size(), &stt);
     if (stt != CRV_OK) return stt;
     cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
     cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
@@ -889,16 +922,46 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
     p->tabAA[j].range = drange;
     p->tabAA[j].nmt = nmt;
   }
-  const size_t na = (size_t)std::max<long long>(amax, 1) * TC_ACHUNK_FLOATS;
-  float* ahi = p->dalloc<float>(na, &stt);
-  float* alo = p->dalloc<float>(na, &stt);
+  p->a_chunks = amax;
   if (stt != CRV_OK) return stt;
-  for (int j = p->J0; j <= p->J; ++j) {
-    p->tabAA[j].hi = ahi;
-    p->tabAA[j].lo = alo;
-  }
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CRV_ECUDA, "contraction table build failed");
   return CRV_OK;
+}
+
+// Per-instance workspace of a plan whose tables exist: f_lm buffers, SHT rows, the (m, n, m')
+// volumes, the ring buffer, the error flag and the per-map A tables of the tensor-core analysis.
+static int alloc_workspace(crv_plan_s* p) {
+  int stt = CRV_OK;
+  const int L = p->L, Mc = p->mc(L), Nc = p->nc(L), N = 2 * L - 1;
+  const size_t el = p->mixed ? sizeof(cx<float>) : sizeof(cx<double>);
+  p->vol_bytes = (size_t)L * p->colset(L).pitch() * el;  // (m, n) planes with pair-interleaved columns
+  p->wflm = p->dalloc<cx<double>>((size_t)L * L, &stt);
+  p->wflm2 = p->dalloc<cx<double>>((size_t)L * L, &stt);
+  p->wflm32 = p->dalloc<cx<float>>((size_t)L * L, &stt);
+  p->wF = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
+  p->wG = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
+  p->wX = p->dalloc<unsigned char>(p->vol_bytes, &stt);
+  // Xb; in the mixed path it also holds the synthesis products Z[m'][mi][l] (L x Mc x L)
+  p->wXb = p->dalloc<unsigned char>(std::max(p->vol_bytes, (size_t)L * Mc * L * el), &stt);
+  p->d_err = p->dalloc<int>(2, &stt);
+  if (stt == CRV_OK) cudaMemset(p->d_err, 0, 2 * sizeof(int));
+  {
+    // ring-chunk buffer: at least one ring, at most all rings, 256 MB (larger chunks: fewer
+    // launches; measured 48 -> 120 MB monotonically faster)
+    const size_t one = (size_t)(N + 1) * std::max(Mc, Nc) * el;
+    p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)256 << 20));
+  }
+  p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
+  if (p->use_tc && stt == CRV_OK) {
+    const size_t na = (size_t)std::max<long long>(p->a_chunks, 1) * TC_ACHUNK_FLOATS;
+    float* ahi = p->dalloc<float>(na, &stt);
+    float* alo = p->dalloc<float>(na, &stt);
+    for (int j = p->J0; j <= p->J && stt == CRV_OK; ++j) {
+      p->tabAA[j].hi = ahi;
+      p->tabAA[j].lo = alo;
+    }
+  }
+  return stt;
 }
 
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule, unsigned flags,
@@ -927,6 +990,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   }
   cudaStream_t st = (cudaStream_t)stream;
   auto* p = new crv_plan_s();
+  p->tabs = std::make_shared<TableSet>();
   p->L = L; p->lambda = lambda; p->J0 = J0; p->J = J; p->spin = spin; p->flags = flags; p->max_batch = max_batch;
   p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
   p->unrot = flags & CRV_F_UNROTATED;
@@ -972,6 +1036,18 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
       }
     }
   }
+  // edge columns d^l_{k,l}(vartheta^j) per scale, for the rotation of Wigner coefficients
+  std::vector<std::vector<double>> edge(J + 1);
+  for (int j = J0; j <= J; ++j) {
+    const int Lb = p->Lj[j], N = 2 * Lb - 1;
+    edge[j].assign((size_t)Lb * N, 0.0);
+    const double th = std::acos(-spin / std::pow(lambda, j));
+    const double sh = spin == 0 ? std::sqrt(0.5) : std::sin(th / 2), ch = spin == 0 ? std::sqrt(0.5) : std::cos(th / 2);
+    for (int l = 0; l < Lb; ++l) {
+      edge_row(l, sh, ch, dp);
+      for (int kk = -l; kk <= l; ++kk) edge[j][(size_t)l * N + (kk + Lb - 1)] = dp[kk + l];
+    }
+  }
   p->nlo.assign(J + 1, 0);
   for (int j = J0; j <= J; ++j) {
     int l = std::abs(spin);
@@ -993,54 +1069,38 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
           if (an >= p->nlo[j] && (std::abs(m) <= an || b_ok)) idx.push_back(i * cs.Nc + ni);
         }
       p->npmap[j] = (int)idx.size();
-      p->dpmap[j] = p->dalloc<int>(idx.size(), &stt);
+      p->dpmap[j] = p->talloc<int>(idx.size(), &stt);
       if (stt == CRV_OK && !idx.empty())
         cudaMemcpy(p->dpmap[j], idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
   }
   // device tables
   const size_t n3 = (size_t)L * L * L;
-  p->dQ = p->dalloc<double>(n3, &stt);
-  if (p->mixed) p->dQ32 = p->dalloc<float>(n3, &stt);
+  p->dQ = p->talloc<double>(n3, &stt);
+  if (p->mixed) p->dQ32 = p->talloc<float>(n3, &stt);
   p->dpsi.assign(J + 1, nullptr);
   p->dpsi32.assign(J + 1, nullptr);
   for (int j = J0; j <= J && stt == CRV_OK; ++j) {
     const size_t ne = p->psi[j].size();
-    p->dpsi[j] = p->dalloc<double>(ne, &stt);
-    p->dpsi32[j] = p->dalloc<float>(ne, &stt);
+    p->dpsi[j] = p->talloc<double>(ne, &stt);
+    p->dpsi32[j] = p->talloc<float>(ne, &stt);
     if (stt != CRV_OK) break;
     std::vector<float> f32(p->psi[j].begin(), p->psi[j].end());
     cudaMemcpy(p->dpsi[j], p->psi[j].data(), ne * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(p->dpsi32[j], f32.data(), ne * sizeof(float), cudaMemcpyHostToDevice);
   }
-  p->dphi = p->dalloc<double>(L, &stt);
+  p->dedge.assign(J + 1, nullptr);
+  for (int j = J0; j <= J && stt == CRV_OK; ++j) {
+    p->dedge[j] = p->talloc<double>(edge[j].size(), &stt);
+    if (stt == CRV_OK) cudaMemcpy(p->dedge[j], edge[j].data(), edge[j].size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  p->dphi = p->talloc<double>(L, &stt);
   if (stt == CRV_OK) cudaMemcpy(p->dphi, p->phi.data(), L * sizeof(double), cudaMemcpyHostToDevice);
   // FFT tables for every band limit in use
   std::set<int> lbs = {L, p->Lphi};
   for (int j = J0; j <= J; ++j) lbs.insert(p->Lj[j]);
   for (int lb : lbs)
     if (stt == CRV_OK) stt = build_fft(p, lb);
-  // workspace
-  const int Mc = p->mc(L), Nc = p->nc(L), N = 2 * L - 1;
-  const size_t el = p->mixed ? sizeof(cx<float>) : sizeof(cx<double>);
-  p->vol_bytes = (size_t)L * p->colset(L).pitch() * el;  // (m, n) planes with pair-interleaved columns
-  p->wflm = p->dalloc<cx<double>>((size_t)L * L, &stt);
-  p->wflm2 = p->dalloc<cx<double>>((size_t)L * L, &stt);
-  p->wflm32 = p->dalloc<cx<float>>((size_t)L * L, &stt);
-  p->wF = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
-  p->wG = p->dalloc<cx<double>>((size_t)L * (2 * L - 1), &stt);
-  p->wX = p->dalloc<unsigned char>(p->vol_bytes, &stt);
-  // Xb; in the mixed path it also holds the synthesis products Z[m'][mi][l] (L x Mc x L)
-  p->wXb = p->dalloc<unsigned char>(std::max(p->vol_bytes, (size_t)L * Mc * L * el), &stt);
-  p->d_err = p->dalloc<int>(2, &stt);
-  if (stt == CRV_OK) cudaMemset(p->d_err, 0, 2 * sizeof(int));
-  {
-    // ring-chunk buffer: at least one ring, at most all rings, 256 MB (larger chunks: fewer
-    // launches; measured 48 -> 120 MB monotonically faster)
-    const size_t one = (size_t)(N + 1) * std::max(Mc, Nc) * el;
-    p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)256 << 20));
-  }
-  p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
   {
     const char* e = getenv("CRV_DISABLE_TC");
     p->use_tc = p->mixed && !p->unrot && !(e && e[0] && e[0] != '0');
@@ -1069,7 +1129,41 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
     const int rc = build_tc_tables(p, st);
     if (rc != CRV_OK) { delete p; return rc; }
   }
+  stt = alloc_workspace(p);
+  if (stt != CRV_OK) { delete p; return stt; }
   *out = p;
+  return CRV_OK;
+}
+
+int crv_plan_clone(crv_plan_t* out, crv_plan_t src, void* stream) {
+  if (!out) return fail(CRV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!src) return fail(CRV_EINVAL, "source plan is NULL");
+  // the same parameters and table pointers (the table set is shared by reference count), a
+  // workspace of its own
+  auto* p = new crv_plan_s(*src);
+  p->allocs.clear();
+  p->bytes = 0;
+  p->wflm = p->wflm2 = nullptr;
+  p->wflm32 = nullptr;
+  p->wF = p->wG = nullptr;
+  p->wX = p->wXb = p->wR = nullptr;
+  p->d_err = nullptr;
+  for (auto& t : p->tabAA) { t.hi = nullptr; t.lo = nullptr; }
+  const int stt = alloc_workspace(p);
+  if (stt != CRV_OK) { delete p; return stt; }
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    delete p;
+    return fail(CRV_ECUDA, "stream synchronisation failed");
+  }
+  *out = p;
+  return CRV_OK;
+}
+
+int crv_plan_bytes(crv_plan_t p, size_t* table_bytes, size_t* workspace_bytes) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (table_bytes) *table_bytes = p->tabs ? p->tabs->bytes : 0;
+  if (workspace_bytes) *workspace_bytes = p->bytes;
   return CRV_OK;
 }
 
@@ -1089,7 +1183,7 @@ int crv_plan_info(crv_plan_t p, int* J, int* Lj, size_t* w_elems, int* L_phi, si
     if (w_elems) w_elems[j] = (j >= p->J0) ? (size_t)Lb * (2 * Lb - 1) * (2 * Lb - 1) : 0;
   }
   if (L_phi) *L_phi = p->Lphi;
-  if (workspace_bytes) *workspace_bytes = p->bytes;
+  if (workspace_bytes) *workspace_bytes = p->bytes + (p->tabs ? p->tabs->bytes : 0);
   return CRV_OK;
 }
 
@@ -1154,6 +1248,35 @@ static int check_batch(crv_plan_t p, int B, const void* a, const void* b) {
   if (!p) return fail(CRV_EINVAL, "plan is NULL");
   if (B < 0 || B > p->max_batch) return fail(CRV_EINVAL, "B must be in [0, max_batch]");
   if (B > 0 && (!a || !b)) return fail(CRV_EINVAL, "null data pointer");
+  return CRV_OK;
+}
+
+static int check_rotate(crv_plan_t p, int j, int B, const void* a, const void* b) {
+  const int s = check_batch(p, B, a, b);
+  if (s) return s;
+  if (j < p->J0 || j > p->J) return fail(CRV_EINVAL, "scale j out of range [J0, J]");
+  return CRV_OK;
+}
+
+int crv_rotate_wigner(crv_plan_t p, int j, const void* wt, void* w, int B, void* stream) {
+  int s = check_rotate(p, j, B, wt, w);
+  if (s) return s;
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  for (int b = 0; b < B; ++b)
+    if (!rotate_wigner_launch(p->dedge[j], Lb, (const cx<double>*)wt + (size_t)b * 2 * Lb * N,
+                              (cx<double>*)w + (size_t)b * Lb * N * N, (cudaStream_t)stream))
+      return CRV_ECUDA;
+  return CRV_OK;
+}
+
+int crv_rotate_wigner_adjoint(crv_plan_t p, int j, const void* w, void* wt, int B, void* stream) {
+  int s = check_rotate(p, j, B, w, wt);
+  if (s) return s;
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  for (int b = 0; b < B; ++b)
+    if (!rotate_wigner_adjoint_launch(p->dedge[j], Lb, (const cx<double>*)w + (size_t)b * Lb * N * N,
+                                      (cx<double>*)wt + (size_t)b * 2 * Lb * N, (cudaStream_t)stream))
+      return CRV_ECUDA;
   return CRV_OK;
 }
 

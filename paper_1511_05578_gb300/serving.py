@@ -7,7 +7,9 @@ and the reconstructed maps go back to the host. Requests arrive over time. The s
 admits a request as soon as a plan for its (L, s) is idle (or another instance fits) and its
 transient buffers fit in the device-memory budget; admitted requests run concurrently, each on
 its own CUDA stream with its own plan instance (a plan serves one stream at a time), and
-completions are detected with CUDA events. Requests that arrive while others run are thereby
+completions are detected with CUDA events. Instances of the same (L, s) share the plan's
+read-only tables (Delta, the tensor-core Delta Psi tables, FFT tables: crv_plan_clone), so a
+second concurrent request of a key costs only a workspace. Requests that arrive while others run are thereby
 admitted as plans and memory free up (continuous batching at request granularity); the queue is
 served first-come first-served, except that a request that does not fit may be passed by later
 ones that do. Band limits the library does not support are rejected at admission.
@@ -42,6 +44,7 @@ class Request:
     status: str = "pending"         # pending | running | done | rejected
     reason: str = ""
     result: object = None           # host array of the reconstructed maps
+    dev_events: object = None       # (start, end) CUDA events of the request's device work
 
 
 def plan_key(req, mixed):
@@ -80,10 +83,15 @@ def percentile(xs, q):
 
 class Scheduler:
     """Admission and accounting. The executor provides:
-        plan_bytes(key) -> bytes a new plan instance of this key would hold
+        plan_bytes(key) -> bytes a new plan instance of this key would add (with tables shared
+                           between instances: the workspace alone once an instance exists)
         create_plan(key) -> plan object (or raises ValueError with a reason when unsupported)
-        destroy_plan(plan)                 frees a plan instance (idle plans are evicted, largest
-                                           first, when a request would not fit otherwise)
+        destroy_plan(plan) -> bytes freed or None (then the bytes it added are assumed); idle
+                           plans are evicted, largest first, when a request would not fit
+                           otherwise
+        freed_bytes(plan) -> bytes destroy_plan would free (optional; default: bytes it added)
+        added_bytes(plan) -> bytes a just-created instance holds beyond what existed (optional;
+                           replaces the estimate plan_bytes gave before it existed)
         start(req, plan) -> handle;  done(handle) -> bool;  finish(handle) -> result
         now() -> seconds
     """
@@ -94,7 +102,7 @@ class Scheduler:
         self.mixed = mixed
         self.max_running = max_running
         self.used = 0                      # bytes held by plans and running requests
-        self.plans = {}                    # key -> list of [plan, busy]
+        self.plans = {}                    # key -> list of [plan, busy, bytes added]
         self.queue = []                    # admitted order: list of requests waiting
         self.running = []                  # (req, plan_entry, handle, bytes)
         self.done = []
@@ -125,14 +133,18 @@ class Scheduler:
             # (it fits alone, since need <= budget)
             return "wait"
         if e is None:
+            added = self.ex.plan_bytes(key)
             try:
                 plan = self.ex.create_plan(key)
             except ValueError as err:
                 req.status, req.reason = "rejected", str(err)
                 return "rejected"
-            e = [plan, False]
+            measured = getattr(self.ex, "added_bytes", None)
+            if measured is not None:  # what the new instance actually holds
+                added = measured(plan)
+            e = [plan, False, added]
             self.plans.setdefault(key, []).append(e)
-            self.used += self.ex.plan_bytes(key)
+            self.used += added
         e[1] = True
         self.used += rb
         req.status, req.start = "running", self.ex.now()
@@ -145,14 +157,18 @@ class Scheduler:
         destroy = getattr(self.ex, "destroy_plan", None)
         if destroy is None:
             return False
+        freed_of = getattr(self.ex, "freed_bytes", None)
+
+        def frees(e):
+            return freed_of(e[0]) if freed_of is not None else e[2]
         idle = [(k, e) for k, lst in self.plans.items() for e in lst if not e[1] and e is not keep]
-        idle.sort(key=lambda ke: -self.ex.plan_bytes(ke[0]))
+        idle.sort(key=lambda ke: -frees(ke[1]))
         for k, e in idle:
             if self.used + need <= self.budget:
                 break
             self.plans[k].remove(e)
-            destroy(e[0])
-            self.used -= self.ex.plan_bytes(k)
+            freed = destroy(e[0])
+            self.used -= e[2] if freed is None else freed
             self.evicted += 1
         return self.used + need <= self.budget
 
@@ -237,12 +253,14 @@ class CudaExecutor:
     """Runs requests through the C ABI: one CUDA stream and one plan instance per running
     request, results read back on that stream, completion by CUDA event."""
 
-    def __init__(self, lam=2.0, J0=2, mixed=True):
+    def __init__(self, lam=2.0, J0=2, mixed=True, share_tables=True):
         import torch
         import paper_1511_05578_gb300 as crv
         self.torch, self.crv = torch, crv
         self.lam, self.J0, self.mixed = lam, J0, mixed
-        self._plan_bytes = {}
+        self.share = share_tables
+        self._plan_bytes = {}     # key -> (table bytes, workspace bytes) measured on an instance
+        self._live = {}           # key -> live plan instances (they share one table set)
 
     def flags(self, L, spin):
         c = self.crv
@@ -252,8 +270,11 @@ class CudaExecutor:
         return f
 
     def plan_bytes(self, key):
+        """Bytes the next instance of `key` adds: its workspace when an instance exists (tables
+        shared), tables and workspace otherwise (measured once an instance has existed)."""
         if key in self._plan_bytes:
-            return self._plan_bytes[key]
+            tb, wb = self._plan_bytes[key]
+            return wb if (self.share and self._live.get(key)) else tb + wb
         L, spin, mixed = key
         # estimate before the first instance exists (the plan's own count replaces it once one
         # does): Delta tables (FP64, + FP32, the tensor-core B tables of both directions and the
@@ -262,8 +283,33 @@ class CudaExecutor:
         mc = L if spin == 0 else 2 * L - 1
         return L ** 3 * (8 + (26 if mixed else 0)) * (mc // L) + 2 * L * mc * L * (8 if mixed else 16)
 
+    def _key_of(self, plan):
+        for k, lst in self._live.items():
+            if any(q is plan for q in lst):
+                return k
+        return None
+
+    def freed_bytes(self, plan):
+        """Bytes destroy_plan(plan) would free: its workspace, and the tables when it is the
+        last instance of its key."""
+        k = self._key_of(plan)
+        tb, wb = plan.table_bytes(), plan.own_bytes()
+        return wb + (tb if (k is None or len(self._live[k]) == 1 or not self.share) else 0)
+
+    def added_bytes(self, plan):
+        """Bytes a just-created instance added: its workspace, and the tables if it is the
+        only instance of its key."""
+        k = self._key_of(plan)
+        tb, wb = plan.table_bytes(), plan.own_bytes()
+        return wb + (tb if (k is None or len(self._live[k]) == 1 or not self.share) else 0)
+
     def destroy_plan(self, plan):
+        freed = self.freed_bytes(plan)
+        k = self._key_of(plan)
+        if k is not None:
+            self._live[k] = [q for q in self._live[k] if q is not plan]
         plan.close()
+        return freed
 
     def create_plan(self, key):
         L, spin, mixed = key
@@ -272,8 +318,13 @@ class CudaExecutor:
         J0 = self.J0
         while self.lam ** J0 < abs(spin):  # theta^j needs lambda^J0 >= |s|
             J0 += 1
-        p = self.crv.Plan(L, self.lam, J0, spin, self.flags(L, spin))
-        self._plan_bytes[key] = p.bytes
+        live = self._live.setdefault(key, [])
+        if self.share and live:
+            p = live[0].clone()
+        else:
+            p = self.crv.Plan(L, self.lam, J0, spin, self.flags(L, spin))
+        self._plan_bytes[key] = (p.table_bytes(), p.own_bytes())
+        live.append(p)
         return p
 
     def now(self):
@@ -293,6 +344,8 @@ class CudaExecutor:
         out_host = torch.empty(shape, dtype=torch.float64).pin_memory()
         keep = [s]
         with torch.cuda.stream(s):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(s)
             if req.maps is not None:
                 host = torch.from_numpy(np.ascontiguousarray(req.maps, dtype=np.float64)).pin_memory()
                 dmaps = host.to("cuda", non_blocking=True)
@@ -313,8 +366,9 @@ class CudaExecutor:
                 crv.crv_analysis(plan.handle, dmaps[b:b + 1], W, Wphi, 1, stream=s)
                 crv.crv_synthesis(plan.handle, W, Wphi, dout[b:b + 1], 1, stream=s)
             out_host.copy_(dout, non_blocking=True)
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
+        req.dev_events = (ev0, ev)
         keep += [dmaps, W, Wphi, dout]
         return {"ev": ev, "out": out_host, "keep": keep, "plan": plan, "inputs": dmaps, "stream": s}
 
@@ -360,10 +414,12 @@ def main(argv=None):
             continue
         for sp in spins:
             key = (L, sp, True)
-            if sch.used + ex.plan_bytes(key) + request_bytes(Request(0, L, sp, b1, 0.0)) <= budget:
+            added = ex.plan_bytes(key)
+            if sch.used + added + request_bytes(Request(0, L, sp, b1, 0.0)) <= budget:
                 pl = ex.create_plan(key)
-                sch.plans.setdefault(key, []).append([pl, False])
-                sch.used += ex.plan_bytes(key)
+                added = ex.added_bytes(pl)
+                sch.plans.setdefault(key, []).append([pl, False, added])
+                sch.used += added
     torch.cuda.synchronize()
     reqs = poisson_requests(a.requests, a.rate, Ls, spins, (b0, b1), seed=a.seed)
     wall = run(sch, reqs)

@@ -139,3 +139,61 @@ def test_idle_resident_plans_are_evicted_when_a_request_would_not_fit():
     assert b.start >= a.finish
     assert sch.used == 96 ** 2  # only b's plan stays resident
     assert sch.stats(1.0)["plans_evicted"] == 1
+
+
+class SharingExecutor(FakeExecutor):
+    """Instances of a key share tables of L^2 bytes; each has a workspace of L bytes."""
+
+    def __init__(self):
+        super().__init__()
+        self.live = {}
+
+    def plan_bytes(self, key):
+        return key[0] if self.live.get(key) else key[0] ** 2 + key[0]
+
+    def create_plan(self, key):
+        plan = super().create_plan(key)
+        self.live.setdefault(key, []).append(plan)
+        self.keys = getattr(self, "keys", {})
+        self.keys[id(plan)] = key
+        return plan
+
+    def _key(self, plan):
+        return self.keys[id(plan)]
+
+    def added_bytes(self, plan):
+        k = self._key(plan)
+        return k[0] + (k[0] ** 2 if len(self.live[k]) == 1 else 0)
+
+    def freed_bytes(self, plan):
+        k = self._key(plan)
+        return k[0] + (k[0] ** 2 if len(self.live[k]) == 1 else 0)
+
+    def destroy_plan(self, plan):
+        freed = self.freed_bytes(plan)
+        k = self._key(plan)
+        self.live[k] = [q for q in self.live[k] if q is not plan]
+        super().destroy_plan(plan)
+        return freed
+
+
+def test_shared_tables_admit_concurrent_instances_for_their_workspace():
+    """With tables shared between instances of a key, a second concurrent request of the same
+    key needs only a workspace: two fit at once in a budget that holds one table set, and the
+    accounting returns to the tables alone once everything but one instance is evicted."""
+    ex = SharingExecutor()
+    L = 64
+    rb = S.request_bytes(_req(0, L))
+    budget = L ** 2 + 2 * L + 2 * rb  # one table set, two workspaces, two requests
+    sch = S.Scheduler(ex, budget, max_running=8)
+    reqs = [_req(i, L) for i in range(2)]
+    S.run(sch, reqs)
+    assert len(sch.done) == 2 and all(r.start == 0.0 for r in reqs)
+    assert len(ex.created) == 2
+    assert sch.used == L ** 2 + 2 * L
+    # a request of another key that needs the room evicts both idle instances: the clone frees
+    # its workspace, the last one the tables too, and the accounting comes back to zero + new
+    big = _req(9, 32, B=1)
+    sch.budget = S.request_bytes(big) + 32 ** 2 + 32
+    S.run(sch, [big])
+    assert len(ex.destroyed) == 2 and sch.used == 32 ** 2 + 32
