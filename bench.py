@@ -50,6 +50,13 @@ def parse():
     ap.add_argument("--fp64-sample-maps", type=int, default=1,
                     help="maps timed on the plain FP64 path for the mixed/FP64 speedup (0 = skip)")
     ap.add_argument("--breakdown", action="store_true", help="print per-kernel-kind device time to stderr")
+    ap.add_argument("--batch-calls", action="store_true",
+                    help="one analysis and one synthesis call per step for all B maps (the plan's map workers run "
+                         "them concurrently; small band limits), instead of one call per map")
+    ap.add_argument("--tune", action="store_true", help="create the plan with CRV_F_TUNE (autotuned workers and ring chunks)")
+    ap.add_argument("--serving-requests", type=int, default=24,
+                    help="requests of the serving leg (Poisson arrivals; 0 = skip)")
+    ap.add_argument("--serving-rate", type=float, default=0.5, help="mean arrivals per second of the serving leg")
     return ap.parse_args()
 
 
@@ -306,12 +313,55 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def serving_leg(args):
+    """Continuous-batching serving of round-trip requests (the serving workload: Poisson
+    arrivals, L uniform in {128, 256, 512, 1024, 2048}, spin in {0, 2}, 1-8 maps per request,
+    mixed precision), run after the headline plans are freed. Plans for every (L, spin) are
+    built before the clock (resident plans); instances of a key share their tables. Returns
+    p50/p99 request latency, maps/s over the wall time, requests done and rejected (with the
+    reasons: L = 2048 is beyond this build's band limit)."""
+    import torch
+    from paper_1511_05578_gb300 import serving as S
+    Ls, spins, Bs = [128, 256, 512, 1024, 2048], [0, 2], (1, 8)
+    free = torch.cuda.mem_get_info()[0]
+    budget = 0.9 * free
+    ex = S.CudaExecutor(lam=args.lam, J0=args.J0)
+    sch = S.Scheduler(ex, budget, mixed=True, max_running=4)
+    for L in Ls:
+        if L > S.MAX_L:
+            continue
+        for sp in spins:
+            key = (L, sp, True)
+            if sch.used + ex.plan_bytes(key) + S.request_bytes(S.Request(0, L, sp, Bs[1], 0.0)) <= budget:
+                pl = ex.create_plan(key)
+                added = ex.added_bytes(pl)
+                sch.plans.setdefault(key, []).append([pl, False, added])
+                sch.used += added
+    torch.cuda.synchronize()
+    reqs = S.poisson_requests(args.serving_requests, args.serving_rate, Ls, spins, Bs, seed=0)
+    wall = S.run(sch, reqs)
+    st = sch.stats(wall)
+    out = {"p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"), "maps_per_s": st["maps_per_s"],
+           "admitted": st["requests_done"], "rejected": st["requests_rejected"], "maps_done": st["maps_done"],
+           "wall_s": wall, "plans_evicted": st["plans_evicted"],
+           "rejected_reasons": sorted({r.reason for r in sch.rejected}),
+           "config": {"requests": args.serving_requests, "rate_per_s": args.serving_rate, "Ls": Ls, "spins": spins,
+                      "maps_per_request": list(Bs), "budget_gb": budget / 1e9, "max_running": 4,
+                      "precision": "mixed", "latency": "arrival to reconstructed maps on the host"}}
+    for lst in sch.plans.values():
+        for e in lst:
+            ex.destroy_plan(e[0])
+    return out
+
+
 def config_dict(args):
     return {"workload": f"curvelet analysis+synthesis, {args.B} real spin-0 maps, L={args.L}, lambda={args.lam:g}, "
                         f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}"
                         + (", unrotated curvelets (O(L^3) single-term contraction)" if args.unrotated else ""),
             "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
-            "precision": args.mode, "unrotated": bool(args.unrotated), "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)"}
+            "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.B if args.batch_calls else 1,
+            "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)" if args.L >= 1024 else
+                  "inputs of a step smaller than L2 at this band limit"}
 
 
 # ---------------------------------------------------------------------------
@@ -340,24 +390,28 @@ def main():
     flags = crv.CRV_F_REAL | (crv.CRV_F_MIXED | crv.CRV_F_W_FP32 if args.mode == "mixed" else 0)
     unrot_flag = crv.CRV_F_UNROTATED if args.unrotated else 0
     flags |= unrot_flag
+    if args.tune:
+        flags |= crv.CRV_F_TUNE
+    nb = B if args.batch_calls else 1  # maps per call
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        plan = crv.Plan(L, lam, J0, 0, flags, max_batch=1, stream=stream.cuda_stream)
+        plan = crv.Plan(L, lam, J0, 0, flags, max_batch=nb, stream=stream.cuda_stream)
         # seeded inputs: f_lm on the host -> maps through our inverse SHT (not timed)
         maps = torch.empty((B, L, 2 * L - 1), dtype=torch.float64, device="cuda")
         f1 = plan.flm_tensor(1)
         for b, seed in enumerate(rank_map_seeds(rank, B)):
             f1.copy_(torch.from_numpy(inputs.flm_gaussian(L, seed, real=True)[None]))
             crv.crv_sht_inv(plan.handle, f1, maps[b:b + 1], 1, stream.cuda_stream)
+        tuning = crv.crv_plan_tuning(plan.handle)
         out = torch.empty_like(maps)
-        W = plan.W_tensors(1)
-        Wphi = plan.Wphi_tensor(1)
+        W = plan.W_tensors(nb)
+        Wphi = plan.Wphi_tensor(nb)
     torch.cuda.synchronize()
 
     def step(src, dst):
-        for b in range(B):
-            crv.crv_analysis(plan.handle, src[b:b + 1], W, Wphi, 1, stream.cuda_stream)
-            crv.crv_synthesis(plan.handle, W, Wphi, dst[b:b + 1], 1, stream.cuda_stream)
+        for b in range(0, B, nb):
+            crv.crv_analysis(plan.handle, src[b:b + nb], W, Wphi, nb, stream.cuda_stream)
+            crv.crv_synthesis(plan.handle, W, Wphi, dst[b:b + nb], nb, stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -383,11 +437,11 @@ def main():
     for _ in range(args.steps):
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for b in range(B):  # one step = all B maps; per-map events give the latency distribution
+        for b in range(0, B, nb):  # one step = all B maps; per-call events give the latency distribution
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            crv.crv_analysis(plan.handle, maps[b:b + 1], W, Wphi, 1, stream.cuda_stream)
-            crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + 1], 1, stream.cuda_stream)
+            crv.crv_analysis(plan.handle, maps[b:b + nb], W, Wphi, nb, stream.cuda_stream)
+            crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + nb], nb, stream.cuda_stream)
             e1.record(stream)
             per_map.append((e0, e1))
         b_.record(stream)
@@ -429,7 +483,7 @@ def main():
             for b in range(B):
                 dev_in.copy_(host_in[b:b + 1], non_blocking=True)
                 crv.crv_analysis(plan.handle, dev_in, W, Wphi, 1, stream.cuda_stream)
-                crv.crv_synthesis(plan.handle, W, Wphi, dev_out, 1, stream.cuda_stream)
+                crv.crv_synthesis(plan.handle, W, Wphi, dev_out, 1, stream.cuda_stream)  # one map per call
                 host_out[b:b + 1].copy_(dev_out, non_blocking=True)
         stream.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
@@ -470,7 +524,7 @@ def main():
         per_scale = {}
         for j in range(J0, plan.J + 1):
             ref = W64[j]
-            per_scale[str(j)] = float(torch.linalg.vector_norm(W[j].double() - ref) / torch.linalg.vector_norm(ref))
+            per_scale[str(j)] = float(torch.linalg.vector_norm(W[j][:1].double() - ref) / torch.linalg.vector_norm(ref))
         fp64 = {"maps_per_s": 1000.0 / ms64, "ms_per_map": ms64, "sample_maps": n64,
                 "speedup_mixed_over_fp64": (1000.0 / ms64 and value / world / (1000.0 / ms64)),
                 "roundtrip_rel_l2": rec64, "mixed_vs_fp64_rel_l2_per_scale": per_scale,
@@ -547,7 +601,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
-        "config": config_dict(args), "p50_ms": p50, "p99_ms": p99, "latency_unit": "ms per map (analysis+synthesis)",
+        "config": config_dict(args), "p50_ms": p50, "p99_ms": p99,
+        "latency_unit": "ms per map (analysis+synthesis)" if nb == 1 else f"ms per call of {nb} maps (analysis+synthesis)",
+        "launches_per_map": launches / (args.steps * B), "plan_tuning": tuning,
         "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_map": roof_map,
         "e2e": e2e,
         "fp64_path": fp64, "step_ms": step_ms,
@@ -559,6 +615,16 @@ def main():
                                 "sample": f"FP64 oracle analysis of {info['rings']} rings of the top scale (L_j={L}, "
                                           f"{info['ring_s']:.2f} s per ring), extrapolated by L_j^3 over all rings of "
                                           f"all scales; synthesis taken equal to analysis"}
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        if plan.handle is not None:
+            plan.close()
+        del maps, out, W, Wphi
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        try:
+            line["serving"] = serving_leg(args)
+        except Exception as err:  # the bench line is printed whatever the serving leg does
+            line["serving"] = {"error": f"{type(err).__name__}: {err}"}
     if args.breakdown and rank == 0:
         for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1]):
             sys.stderr.write(f"{k:20s} {v / args.steps:10.2f} ms/step  {kind_n[k] // args.steps:7d} launches/step\n")

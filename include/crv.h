@@ -69,6 +69,9 @@ enum {
   CRV_F_MIXED = 2,  /* split-FP32 contraction on tensor cores and FP32 FFTs; Delta recursion
                        and the synthesis accumulation of f_lm stay FP64 */
   CRV_F_W_FP32 = 4, /* store W_j as float instead of double */
+  CRV_F_TUNE = 16,   /* autotune at creation: time a batch of zero maps for each number of
+                       concurrent map workers (1, 2, 4, 8 up to max_batch) and ring-chunk size
+                       (64 MB, 256 MB) and keep the fastest (crv_plan_tuning reports it) */
   CRV_F_UNROTATED = 8 /* W_j are the coefficients of the unrotated curvelets s-psi~^(j) (Sec. III-A-1),
                          i.e. W~(rho) with W(rho) = W~(rho rho*), rho* = (0, vartheta^j, 0) (Eq.
                          rotateWigner). Their Wigner coefficients vanish unless |n| = l (Eq.
@@ -86,8 +89,12 @@ enum {
  *   spin      s; CRV_F_REAL requires s = 0
  *   nrule     CRV_NRULE_CURVELET
  *   flags     CRV_F_* bits
- *   max_batch largest B accepted by the transform calls (workspace is per map, so this
- *             only bounds argument checks)
+ *   max_batch largest B accepted by the transform calls. When max_batch > 1 and one map's
+ *             workspace is small (<= 1 GB, L <= 256: the band limits whose kernels cannot fill
+ *             the GPU one map at a time), the plan also holds up to 3 (CRV_F_TUNE: 7) worker instances
+ *             sharing its tables, each with a workspace and a stream of its own: the B maps of
+ *             a call run on up to 4 workers at once (map b on worker b mod K), forked from the
+ *             call's stream and joined back into it by events, so calls stay stream-ordered
  *   stream    CUDA stream used for the table build (Delta recursion)
  * Builds the radial kernels kappa^(j) and scaling function (Sec. II-B), the rotated
  * directional components zeta^(j) (Eq. after directionality_normalisation; with
@@ -111,8 +118,14 @@ int crv_plan_destroy(crv_plan_t plan);
 int crv_plan_clone(crv_plan_t* out, crv_plan_t src, void* stream);
 
 /* Device bytes of a plan: table_bytes of its (shared) read-only tables, workspace_bytes of its
- * own workspace. Either pointer may be NULL. A clone adds workspace_bytes to the device. */
+ * own workspace (its workers' included). Either pointer may be NULL. A clone adds
+ * workspace_bytes to the device. */
 int crv_plan_bytes(crv_plan_t plan, size_t* table_bytes, size_t* workspace_bytes);
+
+/* Launch settings of a plan: the number of map workers a call uses, the ring-chunk size of the
+ * SO(3) ring transforms, and whether the autotuner (CRV_F_TUNE) chose them. Any pointer may be
+ * NULL. */
+int crv_plan_tuning(crv_plan_t plan, int* workers, size_t* ring_bytes, int* tuned);
 
 /* Sizes of a plan. Any output pointer may be NULL.
  *   J                 largest scale

@@ -14,8 +14,8 @@ import os
 
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
-    "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CrvError",
-    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
+    "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CRV_F_TUNE", "CrvError",
+    "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_tuning", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
     "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_rotate_wigner", "crv_rotate_wigner_adjoint", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
     "crv_launch_count", "crv_profile_enable", "crv_profile_kinds", "crv_profile_read", "crv_profile_reset",
@@ -24,7 +24,7 @@ __all__ = [
 
 CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED = range(6)
 CRV_NRULE_CURVELET = 0
-CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED = 1, 2, 4, 8
+CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED, CRV_F_TUNE = 1, 2, 4, 8, 16
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -55,6 +55,7 @@ def load():
         "crv_plan_destroy": (i, [vp]),
         "crv_plan_clone": (i, [ctypes.POINTER(vp), vp, vp]),
         "crv_plan_bytes": (i, [vp, ctypes.POINTER(sz), ctypes.POINTER(sz)]),
+        "crv_plan_tuning": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i)]),
         "crv_plan_info": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(sz), ctypes.POINTER(i),
                               ctypes.POINTER(sz)]),
         "crv_plan_check": (i, [vp]),
@@ -181,6 +182,14 @@ def crv_plan_bytes(plan):
     t, w = ctypes.c_size_t(), ctypes.c_size_t()
     _check(load().crv_plan_bytes(plan, ctypes.byref(t), ctypes.byref(w)))
     return t.value, w.value
+
+
+def crv_plan_tuning(plan):
+    """{'workers', 'ring_bytes', 'tuned'}: the plan's launch settings."""
+    w, t = ctypes.c_int(), ctypes.c_int()
+    r = ctypes.c_size_t()
+    _check(load().crv_plan_tuning(plan, ctypes.byref(w), ctypes.byref(r), ctypes.byref(t)))
+    return {"workers": w.value, "ring_bytes": r.value, "tuned": bool(t.value)}
 
 
 def crv_plan_info(plan):

@@ -271,6 +271,15 @@ struct crv_plan_s {
   std::shared_ptr<TableSet> tabs;  // read-only tables, shared with clones
   std::vector<void*> allocs;       // this instance's workspace
   size_t bytes = 0;
+  // Maps of one call run concurrently on worker instances: clones of this plan (shared tables,
+  // own workspace), each on a stream of its own forked from the caller's stream by an event
+  // and joined back into it (workers[w - 1] on wstreams[w - 1]; worker 0 is the plan itself).
+  std::vector<crv_plan_s*> workers;
+  std::vector<cudaStream_t> wstreams;
+  std::vector<cudaEvent_t> wdone;
+  cudaEvent_t fork_ev = nullptr;
+  int nworkers = 1;                // workers a call uses (<= 1 + workers.size())
+  bool tuned = false;              // nworkers and ring_bytes chosen by the autotuner
 
   static void* raw_alloc(size_t b, int* status) {
     void* p = nullptr;
@@ -302,6 +311,10 @@ struct crv_plan_s {
     return (P*)p;
   }
   ~crv_plan_s() {
+    for (crv_plan_s* w : workers) delete w;
+    for (cudaStream_t st : wstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t e : wdone) cudaEventDestroy(e);
+    if (fork_ev) cudaEventDestroy(fork_ev);
     for (void* p : allocs) cudaFree(p);
   }
   int mc(int Lb) const { return real ? Lb : 2 * Lb - 1; }
@@ -964,6 +977,157 @@ static int alloc_workspace(crv_plan_s* p) {
   return stt;
 }
 
+// A second instance of a plan: the same parameters and table pointers (the table set is
+// shared by reference count), a workspace of its own, no workers.
+static crv_plan_s* clone_instance(const crv_plan_s* src, int* status) {
+  auto* p = new crv_plan_s(*src);
+  p->allocs.clear();
+  p->bytes = 0;
+  p->workers.clear();
+  p->wstreams.clear();
+  p->wdone.clear();
+  p->fork_ev = nullptr;
+  p->nworkers = 1;
+  p->wflm = p->wflm2 = nullptr;
+  p->wflm32 = nullptr;
+  p->wF = p->wG = nullptr;
+  p->wX = p->wXb = p->wR = nullptr;
+  p->d_err = nullptr;
+  for (auto& t : p->tabAA) { t.hi = nullptr; t.lo = nullptr; }
+  *status = alloc_workspace(p);
+  if (*status != CRV_OK) { delete p; return nullptr; }
+  return p;
+}
+
+// n worker instances (clones) with their streams and events; use `use` of the 1 + n workers.
+static int add_workers(crv_plan_s* p, int n, int use) {
+  int stt = CRV_OK;
+  for (int w = 0; w < n && stt == CRV_OK; ++w) {
+    crv_plan_s* q = clone_instance(p, &stt);
+    if (!q) break;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (st) cudaStreamDestroy(st);
+      delete q;
+      return fail(CRV_ECUDA, "worker stream or event creation failed");
+    }
+    p->workers.push_back(q);
+    p->wstreams.push_back(st);
+    p->wdone.push_back(ev);
+  }
+  if (stt != CRV_OK) return stt;
+  if (!p->fork_ev && cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CRV_ECUDA, "event creation failed");
+  }
+  p->nworkers = std::max(1, std::min(use, 1 + (int)p->workers.size()));
+  return CRV_OK;
+}
+
+// Run per_map(instance, b, stream) for the B maps of a call: map b on worker b mod K, each
+// worker's maps in order on its stream; the workers' streams start after the work already
+// queued on st and st continues after all of them (events), so the call stays stream-ordered
+// (and capturable into a CUDA graph) for the caller.
+}  // extern "C"
+template <class F>
+static int run_maps(crv_plan_s* p, int B, cudaStream_t st, F&& per_map) {
+  const int K = std::min(B, p->nworkers);
+  if (K <= 1) {
+    for (int b = 0; b < B; ++b)
+      if (!per_map(p, b, st)) return CRV_ECUDA;
+    return CRV_OK;
+  }
+  if (cudaEventRecord(p->fork_ev, st) != cudaSuccess) return fail(CRV_ECUDA, "fork event record failed");
+  int rc = CRV_OK;
+  for (int w = 0; w < K; ++w) {
+    crv_plan_s* q = w == 0 ? p : p->workers[w - 1];
+    cudaStream_t s = w == 0 ? st : p->wstreams[w - 1];
+    if (w > 0 && cudaStreamWaitEvent(s, p->fork_ev, 0) != cudaSuccess) return fail(CRV_ECUDA, "fork wait failed");
+    for (int b = w; b < B && rc == CRV_OK; b += K)
+      if (!per_map(q, b, s)) rc = CRV_ECUDA;
+    if (w > 0) cudaEventRecord(p->wdone[w - 1], s);
+  }
+  for (int w = 1; w < K; ++w) cudaStreamWaitEvent(st, p->wdone[w - 1], 0);
+  return rc;
+}
+extern "C" {
+
+static void set_ring_bytes(crv_plan_s* p, size_t b) {
+  p->ring_bytes = b;
+  for (crv_plan_s* w : p->workers) w->ring_bytes = b;
+}
+
+// Autotuner (CRV_F_TUNE): time an analysis + synthesis of a batch of zero maps (the work of
+// every kernel does not depend on the values) for each number of workers (1, 2, 4, 8 up to
+// the batch) and ring-chunk size (64 MB and the default 256 MB, where the rings exceed 64 MB),
+// and keep the fastest in the plan. The batch and its coefficients are allocated for the run
+// and freed after it.
+static int tune_plan(crv_plan_s* p, cudaStream_t st) {
+  const int B = std::min(p->max_batch, 1 + (int)p->workers.size());
+  const int L = p->L;
+  const size_t me = (size_t)L * (2 * L - 1) * (p->real ? 1 : 2);
+  const size_t wel = p->wfp32 ? sizeof(float) : sizeof(double);
+  size_t wtot = 0;
+  std::vector<size_t> woff(p->J + 1, 0);
+  for (int j = p->J0; j <= p->J; ++j) {
+    const size_t N = 2 * (size_t)p->Lj[j] - 1;
+    woff[j] = wtot;
+    wtot += (size_t)B * p->Lj[j] * N * N * (p->real ? 1 : 2) * wel;
+  }
+  const size_t pe = (size_t)p->Lphi * (2 * p->Lphi - 1) * (p->real ? 1 : 2);
+  void *maps = nullptr, *W = nullptr, *Wphi = nullptr;
+  if (cudaMalloc(&maps, 2 * B * me * sizeof(double)) != cudaSuccess || cudaMalloc(&W, std::max<size_t>(wtot, 16)) != cudaSuccess ||
+      cudaMalloc(&Wphi, B * pe * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(maps);
+    cudaFree(W);
+    return fail(CRV_ENOMEM, "autotuner: no device memory for its trial batch");
+  }
+  cudaMemsetAsync(maps, 0, 2 * B * me * sizeof(double), st);
+  std::vector<void*> Wj(p->J + 1, nullptr);
+  for (int j = p->J0; j <= p->J; ++j) Wj[j] = (char*)W + woff[j];
+  double* out = (double*)maps + B * me;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  std::vector<int> ks;
+  for (int k = 1; k <= B; k *= 2) ks.push_back(k);
+  std::vector<size_t> rings = {p->ring_bytes};
+  const size_t small = (size_t)64 << 20;
+  if (p->ring_bytes > small) rings.push_back(small);
+  float best = 1e30f;
+  int bestk = p->nworkers;
+  size_t bestr = p->ring_bytes;
+  int rc = CRV_OK;
+  for (size_t rb : rings)
+    for (int k : ks) {
+      p->nworkers = k;
+      set_ring_bytes(p, rb);
+      float ms = 0;
+      for (int rep = 0; rep < 3 && rc == CRV_OK; ++rep) {  // first run warms up
+        if (rep == 1) cudaEventRecord(a, st);
+        rc = crv_analysis(p, maps, Wj.data(), Wphi, B, st);
+        if (rc == CRV_OK) rc = crv_synthesis(p, Wj.data(), Wphi, out, B, st);
+      }
+      cudaEventRecord(b, st);
+      if (rc != CRV_OK || cudaEventSynchronize(b) != cudaSuccess) { rc = rc ? rc : CRV_ECUDA; break; }
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) { best = ms; bestk = k; bestr = rb; }
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(maps);
+  cudaFree(W);
+  cudaFree(Wphi);
+  p->nworkers = bestk;
+  set_ring_bytes(p, bestr);
+  p->tuned = true;
+  return rc;
+}
+
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule, unsigned flags,
                     int max_batch, void* stream) {
   if (!out) return fail(CRV_EINVAL, "out is NULL");
@@ -974,7 +1138,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
   if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");
   if (nrule != CRV_NRULE_CURVELET) return fail(CRV_EINVAL, "unknown nrule");
-  if (flags & ~15u) return fail(CRV_EINVAL, "unknown flag bits");
+  if (flags & ~31u) return fail(CRV_EINVAL, "unknown flag bits");
   if ((flags & CRV_F_REAL) && spin != 0) return fail(CRV_EINVAL, "CRV_F_REAL requires spin 0");
   if (max_batch < 1) return fail(CRV_EINVAL, "max_batch must be >= 1");
   int J = 0;
@@ -1131,6 +1295,18 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   }
   stt = alloc_workspace(p);
   if (stt != CRV_OK) { delete p; return stt; }
+  // workers for the maps of a call: up to 4 when a batch is allowed and an instance's workspace
+  // is at most 1 GB (L <= 256: the band limits whose kernels are too short to fill the GPU one
+  // map at a time)
+  const int kmax = (flags & CRV_F_TUNE) ? 8 : 4;
+  if (max_batch > 1 && p->bytes <= ((size_t)1 << 30)) {
+    stt = add_workers(p, std::min(max_batch, kmax) - 1, std::min(max_batch, 4));
+    if (stt != CRV_OK) { delete p; return stt; }
+  }
+  if (flags & CRV_F_TUNE) {
+    stt = tune_plan(p, st);
+    if (stt != CRV_OK) { delete p; return stt; }
+  }
   *out = p;
   return CRV_OK;
 }
@@ -1139,19 +1315,13 @@ int crv_plan_clone(crv_plan_t* out, crv_plan_t src, void* stream) {
   if (!out) return fail(CRV_EINVAL, "out is NULL");
   *out = nullptr;
   if (!src) return fail(CRV_EINVAL, "source plan is NULL");
-  // the same parameters and table pointers (the table set is shared by reference count), a
-  // workspace of its own
-  auto* p = new crv_plan_s(*src);
-  p->allocs.clear();
-  p->bytes = 0;
-  p->wflm = p->wflm2 = nullptr;
-  p->wflm32 = nullptr;
-  p->wF = p->wG = nullptr;
-  p->wX = p->wXb = p->wR = nullptr;
-  p->d_err = nullptr;
-  for (auto& t : p->tabAA) { t.hi = nullptr; t.lo = nullptr; }
-  const int stt = alloc_workspace(p);
-  if (stt != CRV_OK) { delete p; return stt; }
+  int stt = CRV_OK;
+  crv_plan_s* p = clone_instance(src, &stt);
+  if (!p) return stt;
+  if (src->workers.size() > 0) {
+    stt = add_workers(p, (int)src->workers.size(), src->nworkers);
+    if (stt != CRV_OK) { delete p; return stt; }
+  }
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
     delete p;
     return fail(CRV_ECUDA, "stream synchronisation failed");
@@ -1160,10 +1330,22 @@ int crv_plan_clone(crv_plan_t* out, crv_plan_t src, void* stream) {
   return CRV_OK;
 }
 
+int crv_plan_tuning(crv_plan_t p, int* workers, size_t* ring_bytes, int* tuned) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (workers) *workers = p->nworkers;
+  if (ring_bytes) *ring_bytes = p->ring_bytes;
+  if (tuned) *tuned = p->tuned ? 1 : 0;
+  return CRV_OK;
+}
+
 int crv_plan_bytes(crv_plan_t p, size_t* table_bytes, size_t* workspace_bytes) {
   if (!p) return fail(CRV_EINVAL, "plan is NULL");
   if (table_bytes) *table_bytes = p->tabs ? p->tabs->bytes : 0;
-  if (workspace_bytes) *workspace_bytes = p->bytes;
+  if (workspace_bytes) {
+    size_t w = p->bytes;
+    for (crv_plan_s* q : p->workers) w += q->bytes;
+    *workspace_bytes = w;
+  }
   return CRV_OK;
 }
 
@@ -1183,7 +1365,11 @@ int crv_plan_info(crv_plan_t p, int* J, int* Lj, size_t* w_elems, int* L_phi, si
     if (w_elems) w_elems[j] = (j >= p->J0) ? (size_t)Lb * (2 * Lb - 1) * (2 * Lb - 1) : 0;
   }
   if (L_phi) *L_phi = p->Lphi;
-  if (workspace_bytes) *workspace_bytes = p->bytes + (p->tabs ? p->tabs->bytes : 0);
+  if (workspace_bytes) {
+    size_t w = p->bytes + (p->tabs ? p->tabs->bytes : 0);
+    for (crv_plan_s* q : p->workers) w += q->bytes;
+    *workspace_bytes = w;
+  }
   return CRV_OK;
 }
 
@@ -1191,27 +1377,38 @@ int crv_plan_check(crv_plan_t p) {
   if (!p) return fail(CRV_EINVAL, "plan is NULL");
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
-  int h = 0;
-  cudaMemcpy(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-  if (h) {
-    cudaMemset(p->d_err, 0, sizeof(int));
-    return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
+  int any = 0;
+  for (size_t w = 0; w <= p->workers.size(); ++w) {
+    crv_plan_s* q = w == 0 ? p : p->workers[w - 1];
+    int h = 0;
+    cudaMemcpy(&h, q->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (h) {
+      cudaMemset(q->d_err, 0, sizeof(int));
+      any = 1;
+    }
   }
+  if (any) return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
   return CRV_OK;
 }
 
 int crv_plan_check_stream(crv_plan_t p, void* stream) {
   if (!p) return fail(CRV_EINVAL, "plan is NULL");
   cudaStream_t st = (cudaStream_t)stream;
-  int h = 0;
-  cudaError_t e = cudaMemcpyAsync(&h, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
-  if (h) {
-    cudaMemsetAsync(p->d_err, 0, sizeof(int), st);
-    cudaStreamSynchronize(st);
-    return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
+  int any = 0;
+  // the workers' streams were joined into st by the calls, so st orders their flags too
+  for (size_t w = 0; w <= p->workers.size(); ++w) {
+    crv_plan_s* q = w == 0 ? p : p->workers[w - 1];
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, q->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
+    if (h) {
+      cudaMemsetAsync(q->d_err, 0, sizeof(int), st);
+      cudaStreamSynchronize(st);
+      any = 1;
+    }
   }
+  if (any) return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
   return CRV_OK;
 }
 
@@ -1284,63 +1481,56 @@ int crv_sht_fwd(crv_plan_t p, const void* map, void* flm, int B, void* stream) {
   int s = check_batch(p, B, map, flm);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
-  for (int b = 0; b < B; ++b)
-    if (!sht_forward(p, (const double*)map + b * me, (cx<double>*)flm + (size_t)b * p->L * p->L, p->L, p->spin,
-                     p->real, (cudaStream_t)stream))
-      return CRV_ECUDA;
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return sht_forward(q, (const double*)map + b * me, (cx<double>*)flm + (size_t)b * q->L * q->L, q->L, q->spin,
+                       q->real, st);
+  });
 }
 
 int crv_sht_inv(crv_plan_t p, const void* flm, void* map, int B, void* stream) {
   int s = check_batch(p, B, flm, map);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
-  for (int b = 0; b < B; ++b)
-    if (!sht_inverse(p, (const cx<double>*)flm + (size_t)b * p->L * p->L, (double*)map + b * me, p->L, p->spin,
-                     p->real, (cudaStream_t)stream))
-      return CRV_ECUDA;
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return sht_inverse(q, (const cx<double>*)flm + (size_t)b * q->L * q->L, (double*)map + b * me, q->L, q->spin,
+                       q->real, st);
+  });
 }
 
 int crv_analysis_lm(crv_plan_t p, const void* flm, void* const* W, void* Wphi, int B, void* stream) {
   int s = check_batch(p, B, flm, W);
   if (s) return s;
-  for (int b = 0; b < B; ++b)
-    if (!do_analysis(p, (const cx<double>*)flm + (size_t)b * p->L * p->L, W, b, (double*)Wphi, (cudaStream_t)stream))
-      return CRV_ECUDA;
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return do_analysis(q, (const cx<double>*)flm + (size_t)b * q->L * q->L, W, b, (double*)Wphi, st);
+  });
 }
 
 int crv_analysis(crv_plan_t p, const void* map, void* const* W, void* Wphi, int B, void* stream) {
   int s = check_batch(p, B, map, W);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
-  for (int b = 0; b < B; ++b) {
-    if (!sht_forward(p, (const double*)map + b * me, p->wflm, p->L, p->spin, p->real, (cudaStream_t)stream))
-      return CRV_ECUDA;
-    if (!do_analysis(p, p->wflm, W, b, (double*)Wphi, (cudaStream_t)stream)) return CRV_ECUDA;
-  }
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return sht_forward(q, (const double*)map + b * me, q->wflm, q->L, q->spin, q->real, st) &&
+           do_analysis(q, q->wflm, W, b, (double*)Wphi, st);
+  });
 }
 
 int crv_synthesis_lm(crv_plan_t p, const void* const* W, const void* Wphi, void* flm, int B, void* stream) {
   int s = check_batch(p, B, W, flm);
   if (s) return s;
-  for (int b = 0; b < B; ++b)
-    if (!do_synthesis(p, W, b, (const double*)Wphi, (cx<double>*)flm + (size_t)b * p->L * p->L, (cudaStream_t)stream))
-      return CRV_ECUDA;
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return do_synthesis(q, W, b, (const double*)Wphi, (cx<double>*)flm + (size_t)b * q->L * q->L, st);
+  });
 }
 
 int crv_synthesis(crv_plan_t p, const void* const* W, const void* Wphi, void* map, int B, void* stream) {
   int s = check_batch(p, B, W, map);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
-  for (int b = 0; b < B; ++b) {
-    if (!do_synthesis(p, W, b, (const double*)Wphi, p->wflm, (cudaStream_t)stream)) return CRV_ECUDA;
-    if (!sht_inverse(p, p->wflm, (double*)map + b * me, p->L, p->spin, p->real, (cudaStream_t)stream)) return CRV_ECUDA;
-  }
-  return CRV_OK;
+  return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
+    return do_synthesis(q, W, b, (const double*)Wphi, q->wflm, st) &&
+           sht_inverse(q, q->wflm, (double*)map + b * me, q->L, q->spin, q->real, st);
+  });
 }
 
 }  // extern "C"

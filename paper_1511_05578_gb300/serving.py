@@ -27,6 +27,12 @@ import numpy as np
 from . import inputs
 
 MAX_L = 1024  # crv_plan_create returns CRV_EUNSUPPORTED above this band limit
+BATCH_L = 256  # up to this band limit a request's maps go through one call (the plan's map
+MAX_B = 8      # workers run them concurrently); above it one map per call reuses one W
+
+
+class NoMemory(Exception):
+    """A plan instance could not be allocated now (device memory held by others)."""
 
 
 @dataclass
@@ -67,11 +73,27 @@ def w_bytes(L, spin, lam=2.0, J0=2, w_fp32=True):
     return tot
 
 
+def plan_estimate(L, spin, mixed=True):
+    """Device bytes of a first plan instance before one exists (tables + workspace), from the
+    library's allocations: Delta^l(pi/2) for l < L (L^3 doubles, and floats when mixed); the
+    tensor-core Delta Psi tables of both directions (about 17 L^2 Nc bytes over all scales);
+    two (m, n, m') volumes; the per-map A tables of the tensor-core analysis; the ring buffer.
+    m runs over L values (real spin 0) or 2L - 1; n over about L (spin 0: even n) or 2L - 1."""
+    mc = L if spin == 0 else 2 * L - 1
+    nc = L if spin == 0 else 2 * L - 1
+    ring = min(L * (2 * L) * max(mc, nc) * (8 if mixed else 16), 256 << 20)
+    if mixed:
+        return 12 * L ** 3 + 17.2 * L * L * nc + 2 * 8 * L * mc * nc + 8 * L * L * mc + ring
+    return 8 * L ** 3 + 2 * 16 * L * mc * nc + ring
+
+
 def request_bytes(req, w_fp32=True):
-    """Transient device bytes of a request: one map's W (maps are processed one after the other
-    and W is reused) plus the B input and B output maps and the scaling coefficients."""
+    """Transient device bytes of a request: the coefficients W of one map (maps processed one
+    after the other, W reused), or of all B maps when they go through one call (L <= BATCH_L),
+    plus the B input and B output maps and the scaling coefficients."""
     mapb = req.L * (2 * req.L - 1) * 8 * (1 if req.spin == 0 else 2)
-    return w_bytes(req.L, req.spin, w_fp32=w_fp32) + 2 * req.B * mapb + 2 * mapb
+    nw = req.B if req.L <= BATCH_L else 1
+    return nw * w_bytes(req.L, req.spin, w_fp32=w_fp32) + 2 * req.B * mapb + 2 * nw * mapb
 
 
 def percentile(xs, q):
@@ -139,6 +161,17 @@ class Scheduler:
             except ValueError as err:
                 req.status, req.reason = "rejected", str(err)
                 return "rejected"
+            except NoMemory as err:
+                # the estimate was short: free every idle plan and try once more, else wait for
+                # the running requests (or reject when nothing else holds memory)
+                self._evict_idle(self.budget + 1)
+                try:
+                    plan = self.ex.create_plan(key)
+                except NoMemory:
+                    if self.running:
+                        return "wait"
+                    req.status, req.reason = "rejected", f"no device memory for the plan: {err}"
+                    return "rejected"
             measured = getattr(self.ex, "added_bytes", None)
             if measured is not None:  # what the new instance actually holds
                 added = measured(plan)
@@ -280,8 +313,7 @@ class CudaExecutor:
         # does): Delta tables (FP64, + FP32, the tensor-core B tables of both directions and the
         # per-map A tables when mixed) and the two (m, n, m') workspaces, complex, m over
         # 2L - 1 values for spin != 0
-        mc = L if spin == 0 else 2 * L - 1
-        return L ** 3 * (8 + (26 if mixed else 0)) * (mc // L) + 2 * L * mc * L * (8 if mixed else 16)
+        return plan_estimate(L, spin, mixed)
 
     def _key_of(self, plan):
         for k, lst in self._live.items():
@@ -319,10 +351,15 @@ class CudaExecutor:
         while self.lam ** J0 < abs(spin):  # theta^j needs lambda^J0 >= |s|
             J0 += 1
         live = self._live.setdefault(key, [])
-        if self.share and live:
-            p = live[0].clone()
-        else:
-            p = self.crv.Plan(L, self.lam, J0, spin, self.flags(L, spin))
+        try:
+            if self.share and live:
+                p = live[0].clone()
+            else:
+                p = self.crv.Plan(L, self.lam, J0, spin, self.flags(L, spin), max_batch=MAX_B if L <= BATCH_L else 1)
+        except self.crv.CrvError as err:
+            if err.status == self.crv.CRV_ENOMEM:
+                raise NoMemory(str(err)) from err
+            raise
         self._plan_bytes[key] = (p.table_bytes(), p.own_bytes())
         live.append(p)
         return p
@@ -359,12 +396,13 @@ class CudaExecutor:
                 for b in range(req.B):
                     crv.crv_sht_inv(plan.handle, fd[b:b + 1], dmaps[b:b + 1], 1, stream=s)
                 keep += [fh, fd]
-            W = plan.W_tensors(1)
-            Wphi = plan.Wphi_tensor(1)
+            nb = req.B if (req.L <= BATCH_L and req.B <= plan.max_batch) else 1  # maps per call
+            W = plan.W_tensors(nb)
+            Wphi = plan.Wphi_tensor(nb)
             dout = torch.empty_like(dmaps)
-            for b in range(req.B):
-                crv.crv_analysis(plan.handle, dmaps[b:b + 1], W, Wphi, 1, stream=s)
-                crv.crv_synthesis(plan.handle, W, Wphi, dout[b:b + 1], 1, stream=s)
+            for b in range(0, req.B, nb):
+                crv.crv_analysis(plan.handle, dmaps[b:b + nb], W, Wphi, nb, stream=s)
+                crv.crv_synthesis(plan.handle, W, Wphi, dout[b:b + nb], nb, stream=s)
             out_host.copy_(dout, non_blocking=True)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
