@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--batch-calls", action="store_true",
                     help="one analysis and one synthesis call per step for all B maps (the plan's map workers run "
                          "them concurrently; small band limits), instead of one call per map")
+    ap.add_argument("--maps-per-call", type=int, default=1, help="maps per analysis/synthesis call (a divisor of B)")
     ap.add_argument("--tune", action="store_true", help="create the plan with CRV_F_TUNE (autotuned workers and ring chunks)")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving leg (Poisson arrivals; 0 = skip)")
@@ -359,7 +360,7 @@ def config_dict(args):
                         f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}"
                         + (", unrotated curvelets (O(L^3) single-term contraction)" if args.unrotated else ""),
             "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
-            "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.B if args.batch_calls else 1,
+            "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.B if args.batch_calls else max(1, args.maps_per_call),
             "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)" if args.L >= 1024 else
                   "inputs of a step smaller than L2 at this band limit"}
 
@@ -392,7 +393,7 @@ def main():
     flags |= unrot_flag
     if args.tune:
         flags |= crv.CRV_F_TUNE
-    nb = B if args.batch_calls else 1  # maps per call
+    nb = B if args.batch_calls else max(1, args.maps_per_call)  # maps per call
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         plan = crv.Plan(L, lam, J0, 0, flags, max_batch=nb, stream=stream.cuda_stream)

@@ -466,6 +466,28 @@ static bool set_smem(K kernel, size_t bytes) {
   return func_attr_once((const void*)kernel, (int)bytes);
 }
 
+// Shared-memory carveout of a kernel set to what `blocks` resident blocks of `bytes` each need
+// (and no more), so that the rest of the SM's unified L1/shared storage stays L1: the ring
+// transforms' strided loads depend on L1 capacity. Once per kernel and device.
+static void carveout_for(const void* kernel, size_t bytes, int blocks) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static std::set<std::pair<const void*, int>> done;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  if (done.count({kernel, dev})) return;
+  int maxsm = 0;
+  if (cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || maxsm <= 0) {
+    cudaGetLastError();
+    return;
+  }
+  const size_t need = (size_t)blocks * (bytes + 1024);  // + the per-block reservation
+  const int pct = (int)std::min<size_t>(100, (need * 100 + maxsm - 1) / maxsm);
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+    cudaGetLastError();  // a preference only: the launch works either way
+  done.insert({kernel, dev});
+}
+
 static int num_sms() { return device_sms(); }
 
 // Persistent FFT blocks (one or two per SM, by shared memory and registers), each
@@ -478,6 +500,7 @@ static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld,
   auto kern = dft_kernel<T, NT, COLS, PT, Ld, St>;
   if (!set_smem(kern, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
+  carveout_for((const void*)kern, smem, bps);
   const int grid = std::max(1, std::min((nseq + G - 1) / G, num_sms() * bps));
   KTimer kt(kind, s);
   kern<<<grid, NT, smem, s>>>(tb, sign, nseq, ld, st);
@@ -509,7 +532,7 @@ static bool run_beta_synth_nt(const DftTab<T>& tb, int Lb, int ncols, const cx<T
                               int kind, PairMap pm, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
-  const size_t smem = fft_smem_bytes<T>(NT);
+  const size_t smem = fft_smem_bytes_tabs<T>(NT, tb.P, 1);
   if (!set_smem(beta_synth_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
   const int npair = pm.idx ? pm.n : num_col_pairs(cs);
@@ -536,7 +559,7 @@ static bool run_beta_quad_nt(const DftTab<T>& tb, const CorrTab<T>& ct, int Lb, 
                              ColSet cs, T scale, int pa, int pb, int pc, PairMap pm, int kind, cudaStream_t s) {
   const int G = NT / (tb.P / 16);
   if (G < 1) { g_err = "FFT length too large for the block"; return false; }
-  const size_t smem = fft_smem_bytes<T>(NT);
+  const size_t smem = fft_smem_bytes_tabs<T>(NT, tb.P, 2);
   if (!set_smem(beta_quad_kernel<T, NT, PT>, smem)) return false;
   const int bps = FftMinBlocks<T, NT>::value;
   const int npair = pm.idx ? pm.n : num_col_pairs(cs);
@@ -1299,7 +1322,9 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   // is at most 1 GB (L <= 256: the band limits whose kernels are too short to fill the GPU one
   // map at a time)
   const int kmax = (flags & CRV_F_TUNE) ? 8 : 4;
-  if (max_batch > 1 && p->bytes <= ((size_t)1 << 30)) {
+  size_t wlimit = (size_t)1 << 30;
+  if (const char* e = getenv("CRV_WORKER_MAX_GB")) wlimit = (size_t)(atof(e) * (1 << 30));
+  if (max_batch > 1 && p->bytes <= wlimit) {
     stt = add_workers(p, std::min(max_batch, kmax) - 1, std::min(max_batch, 4));
     if (stt != CRV_OK) { delete p; return stt; }
   }

@@ -64,6 +64,32 @@ __device__ __forceinline__ void fft_slot(int& g, int& t, XBuf2<T>& buf, unsigned
   buf.cur = 0;
 }
 
+// The FP32 beta transforms stage the spectra they multiply by (Bluestein's kernel, the weight
+// spectrum of the quadrature) in shared memory after the exchange buffers, once per block: every
+// column pair then reads them there instead of through L1 (and the quadrature no longer spills
+// registers). FP64 blocks have no room left for them.
+template <class T> __host__ __device__ constexpr bool kStageSpectra() { return sizeof(T) == 4; }
+template <class T> __host__ __device__ inline size_t fft_smem_bytes_tabs(int NT, int P, int ntab) {
+  return fft_smem_bytes<T>(NT) + (kStageSpectra<T>() ? (size_t)ntab * P * sizeof(cx<T>) : 0);
+}
+// Copy n tables of P values into the staging area (all threads of the block; ends with a
+// barrier) and return its start; without staging return nullptr.
+template <class T, int NT>
+__device__ __forceinline__ const cx<T>* stage_spectra(unsigned char* smraw, int P, const cx<T>* a,
+                                                      const cx<T>* b = nullptr) {
+  if constexpr (!kStageSpectra<T>()) {
+    return nullptr;
+  } else {
+    cx<T>* s = reinterpret_cast<cx<T>*>(smraw + fft_smem_bytes<T>(NT));
+    for (int i = threadIdx.x; i < P; i += NT) {
+      s[i] = a[i];
+      if (b) s[P + i] = b[i];
+    }
+    __syncthreads();
+    return s;
+  }
+}
+
 // Blocks of NT threads; FP32 blocks of 256 threads fit twice on an SM (<= 128 registers).
 template <class T, int NT> struct FftMinBlocks { static constexpr int value = (sizeof(T) == 4 && NT <= 256) ? 2 : 1; };
 
@@ -77,6 +103,8 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) dft_kernel(D
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, COLS, PT>(g, t, buf, smraw, tb.P);
+  // the kernel spectrum is read through L1 here: the ring transforms' strided loads need the L1
+  // that staging it in shared memory would take (measured: staging it made them 4-15 % slower)
   const cx<T>* __restrict__ kh = (sign < 0) ? tb.khat_f : tb.khat_i;
   const int s_end = nseq, s_step = gridDim.x * G;
   for (int s0 = blockIdx.x * G; s0 < s_end; s0 += s_step) {
@@ -518,6 +546,8 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_k
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
+  const cx<T>* khat = tb.khat_i;
+  if (const cx<T>* st = stage_spectra<T, NT>(smraw, PT ? PT : tb.P, khat)) khat = st;
   const int span = (npair + gridDim.x * G - 1) / (gridDim.x * G) * G;
   const int s_end = min(npair, (blockIdx.x + 1) * span);
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
@@ -533,7 +563,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_synth_k
     }
     fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = v[q] * tb.khat_i[t + q * TP];
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * khat[t + q * TP];
     fft16<+1, false, PT>(v, tb, buf, t);
     const XBuf<T> y = buf.take();
 #pragma unroll
@@ -586,6 +616,12 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
   int g, t;
   XBuf2<T> buf;
   fft_slot<T, NT, true, PT>(g, t, buf, smraw, tb.P);
+  const cx<T>* khat = tb.khat_f;
+  const cx<T>* what = ct.what;
+  if (const cx<T>* st = stage_spectra<T, NT>(smraw, PT ? PT : tb.P, khat, what)) {
+    khat = st;
+    what = st + (PT ? PT : tb.P);
+  }
   const int span = (npair + gridDim.x * G - 1) / (gridDim.x * G) * G;
   const int s_end = min(npair, (blockIdx.x + 1) * span);
   for (int s0 = blockIdx.x * span; s0 < s_end; s0 += G) {
@@ -605,7 +641,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     }
     fft16<-1, true, PT>(v, tb, buf, t);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = v[q] * tb.khat_f[t + q * TP];
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * khat[t + q * TP];
     fft16<+1, false, PT>(v, tb, buf, t);
     // u_{m''} at index m'' mod Q: D_{m'' mod N} h_k e^{-i m'' pi/N} / N; zero for Lb <= index <= Q - Lb
     {
@@ -622,7 +658,7 @@ __global__ void __launch_bounds__(NT, (FftMinBlocks<T, NT>::value)) beta_quad_ke
     }
     fft16<-1, false, PT>(v, tb, buf, t);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = v[q] * ct.what[t + q * TP];
+    for (int q = 0; q < 16; ++q) v[q] = v[q] * what[t + q * TP];
     fft16<+1, false, PT>(v, tb, buf, t);
     // unfold into the two columns
     const XBuf<T> y = buf.take();
