@@ -9,7 +9,8 @@
 //   edge row   Delta^l_{l,n} = (-1)^{l-n} 2^{-l} sqrt(C(2l, l+n))
 //              (the single surviving term of Eq. wigner_sum_reln at beta = pi/2),
 //              built per l by the ratio Delta^l_{l,n+1}/Delta^l_{l,n} = -sqrt((l-n)/(l+n+1))
-//              from 2^{-l} sqrt(C(2l,l)) = prod_k sqrt((2k-1)/(2k));
+//              from 2^{-l} sqrt(C(2l,l)) = prod_k sqrt((2k-1)/(2k)), both products as
+//              row passes (block-wide scans with warp shuffles);
 //   columns    Delta^l_{m,n} = 2n/sqrt((l-m)(l+m+1)) Delta^l_{m+1,n}
 //                - sqrt((l-m-1)(l+m+2)/((l-m)(l+m+1))) Delta^l_{m+2,n},  m = l-1 .. 0.
 // The edge values reach 2^-l, below the double range past l ~ 1022, so every value
@@ -19,24 +20,88 @@
 
 namespace crv {
 
-// One thread per l: seed row (mantissa, exponent) for n = 0..l.
-__global__ void delta_seed_kernel(int L, double* __restrict__ seed_v, int* __restrict__ seed_e) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= L) return;
-  double v = 1.0;
-  int e = 0;
-  for (int k = 1; k <= l; ++k) {  // 2^-l sqrt(C(2l, l)) = prod sqrt((2k-1)/(2k)), stays > 0.05 for l <= 4096
-    v *= sqrt((2.0 * k - 1.0) / (2.0 * k));
+// Products of numbers carried as (mantissa, binary exponent): the edge values fall below the
+// double range past l ~ 1022. mul() renormalises, so a product of many factors keeps the
+// relative precision of a plain double product.
+struct MantExp {
+  double m;
+  int e;
+};
+__device__ __forceinline__ MantExp me_mul(MantExp a, MantExp b) {
+  int k;
+  const double m = frexp(a.m * b.m, &k);
+  return MantExp{m, a.e + b.e + k};
+}
+// Inclusive product scan across the 32 lanes of a warp (row pass by warp shuffles).
+__device__ __forceinline__ MantExp warp_scan_mul(MantExp x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double m = __shfl_up_sync(0xffffffffu, x.m, o);
+    const int e = __shfl_up_sync(0xffffffffu, x.e, o);
+    if (lane >= o) x = me_mul(MantExp{m, e}, x);
   }
-  if (l & 1) v = -v;  // (-1)^{l-n} at n = 0
-  for (int n = 0; n <= l; ++n) {
-    seed_v[(size_t)l * L + n] = v;
-    seed_e[(size_t)l * L + n] = e;
-    if (n < l) {
-      v = -v * sqrt((double)(l - n) / (double)(l + n + 1));
-      int k;
-      v = frexp(v, &k);
-      e += k;
+  return x;
+}
+constexpr int kSeedThreads = 256;
+
+// Block per l: the edge row Delta^l_{l,n}, n = 0..l, as (mantissa, exponent). Its magnitude is
+// |Delta^l_{l,0}| prod_{k<n} r_k with r_k = sqrt((l-k)/(l+k+1)), and |Delta^l_{l,0}| =
+// prod_{k=1..l} sqrt((2k-1)/(2k)) (= 2^-l sqrt(C(2l,l)) >= 0.02 for l < 4096); sign (-1)^{l-n}.
+// Both products run as row passes over the block: per 256 values a warp-shuffle scan in each
+// warp, the warps' totals scanned by warp 0 through shared memory, and a carry into the next
+// 256 values.
+__global__ void __launch_bounds__(kSeedThreads) delta_seed_kernel(int L, double* __restrict__ seed_v,
+                                                                  int* __restrict__ seed_e) {
+  const int l = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = kSeedThreads / 32;
+  __shared__ MantExp wtot[NW];
+  __shared__ MantExp carry;
+  // block-wide inclusive scan of x (all threads call); adds the running carry and advances it
+  auto block_scan = [&](MantExp x) -> MantExp {
+    x = warp_scan_mul(x);
+    if (lane == 31) wtot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      MantExp w = lane < NW ? wtot[lane] : MantExp{1.0, 0};
+      w = warp_scan_mul(w);
+      if (lane < NW) wtot[lane] = w;
+    }
+    __syncthreads();
+    if (wid > 0) x = me_mul(wtot[wid - 1], x);
+    x = me_mul(carry, x);
+    __syncthreads();
+    if (tid == kSeedThreads - 1) carry = x;
+    __syncthreads();
+    return x;
+  };
+  // |Delta^l_{l,0}| = prod_{k=1..l} sqrt((2k-1)/(2k)): the carry after the scan is the product
+  if (tid == 0) carry = MantExp{1.0, 0};
+  __syncthreads();
+  for (int k0 = 1; k0 <= l; k0 += kSeedThreads) {
+    const int k = k0 + tid;
+    MantExp f{1.0, 0};
+    if (k <= l) {
+      int ke;
+      const double m = frexp(sqrt((2.0 * k - 1.0) / (2.0 * k)), &ke);
+      f = MantExp{m, ke};
+    }
+    block_scan(f);
+  }
+  // |Delta^l_{l,n}| = |Delta^l_{l,0}| prod_{k<n} r_k: inclusive scan of the factors f_n = r_{n-1}
+  // (f_0 = 1), starting from the carry |Delta^l_{l,0}|
+  for (int n0 = 0; n0 <= l; n0 += kSeedThreads) {
+    const int n = n0 + tid, k = n - 1;
+    MantExp f{1.0, 0};
+    if (k >= 0 && k < l) {
+      int ke;
+      const double m = frexp(sqrt((double)(l - k) / (double)(l + k + 1)), &ke);
+      f = MantExp{m, ke};
+    }
+    const MantExp v = block_scan(f);
+    if (n <= l) {
+      seed_v[(size_t)l * L + n] = ((l - n) & 1) ? -v.m : v.m;
+      seed_e[(size_t)l * L + n] = v.e;
     }
   }
 }
@@ -91,7 +156,7 @@ cudaError_t build_delta(int L, double* Q, float* q32, double* seed_v, int* seed_
   }
   {
     KTimer kt(K_DELTA, st);
-    delta_seed_kernel<<<(L + 127) / 128, 128, 0, st>>>(L, seed_v, seed_e);
+    delta_seed_kernel<<<L, kSeedThreads, 0, st>>>(L, seed_v, seed_e);
     kt.done();
   }
   if (!launch_ok("delta_seed_kernel")) return cudaErrorLaunchFailure;
