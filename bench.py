@@ -187,27 +187,41 @@ def kind_work(L, lam, J0, el_bytes, w_bytes, unrot=False):
     return w
 
 
-def kernel_source_hash():
-    """Hash of the CUDA sources (csrc/*.cu, *.cuh): recorded DRAM traffic is used only
-    while the kernels are unchanged since the ncu capture that produced it."""
+# The sources that define each kernel kind's device code: recorded DRAM traffic of a kind is
+# used only while these are unchanged since the ncu capture that produced it.
+KIND_SOURCES = {
+    "fft": ["common.cuh", "fft.cuh", "transforms.cuh"],
+    "tc": ["common.cuh", "fft.cuh", "transforms.cuh", "tc_gemm.cuh", "tc_contract.cuh", "tc_contract.cu"],
+}
+
+
+def kernel_source_hash(kind="fft"):
+    """Hash of the CUDA sources that define a kernel kind (`fft` for the DFT and beta kinds,
+    `tc` for the tensor-core contractions)."""
     d = os.path.join(ROOT, "paper_1511_05578_gb300", "csrc")
+    files = KIND_SOURCES["tc" if kind.startswith("tc_") or kind == "tc" else "fft"]
     h = hashlib.sha256()
-    for n in sorted(os.listdir(d)):
-        if n.endswith((".cu", ".cuh")):
-            h.update(n.encode())
-            with open(os.path.join(d, n), "rb") as f:
-                h.update(f.read())
+    for n in files:
+        h.update(n.encode())
+        with open(os.path.join(d, n), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind):
-    """DRAM bytes (read + write) per launch of a kernel kind, averaged over one map's launches
-    in an ncu capture (profiles/traffic.json), or None if absent or taken on other sources."""
+def traffic_workload(L, lam, J0, mode, unrot):
+    """Key of the workload a recorded traffic figure belongs to."""
+    return f"L={L},lambda={float(lam):g},J0={J0},{mode}" + (",unrotated" if unrot else "")
+
+
+def recorded_traffic(kind, workload):
+    """DRAM bytes (read + write) per launch of a kernel kind on a workload (from
+    profiles/traffic.json), or None if absent, recorded for another workload, or taken on
+    other sources of that kind."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     e = json.load(open(p)).get(kind)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kind) or e.get("workload") != workload:
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -539,6 +553,7 @@ def main():
     wb = 4 if args.mode == "mixed" else 8
     work = kind_work(L, lam, J0, el, wb, args.unrotated)
     dom = max(kind_ms, key=kind_ms.get) if kind_ms else None
+    twl = traffic_workload(L, lam, J0, args.mode, args.unrotated)
     roof = None
     if dom:
         avg_ms = kind_ms[dom] / kind_n[dom]
@@ -549,14 +564,14 @@ def main():
             peak = fp32_alu_peak_tflops(clk.get("sm_mhz")) if args.mode == "mixed" else fp64_alu_peak_tflops(clk.get("sm_mhz"))
             ach = flops_launch / (avg_ms * 1e-3) / 1e12
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": recorded_traffic(dom),
+                    "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
                     "peak_src": "FP32 FMA lanes x clock" if args.mode == "mixed" else "FP64 FMA rate measured on this pool"}
         elif dom in ("tc_analysis", "tc_synthesis"):
             flops_launch = flops_map / per_launch_units
             peak = peaks["bf16_tflops_sustained"] / 2.0  # TF32 = bf16 / 2 (nominal ratio)
             ach = flops_launch / (avg_ms * 1e-3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": recorded_traffic(dom),
+                    "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
                     "peak_src": f"{peaks['src']} bf16 sustained / 2 (tf32); achieved counts FP32-accurate flops"}
         else:
             # the DFT kernels are bound by FP32 (FP64) arithmetic, not by HBM: their
@@ -566,7 +581,7 @@ def main():
             peak = fp32_alu_peak_tflops(clk.get("sm_mhz")) if args.mode == "mixed" else fp64_alu_peak_tflops(clk.get("sm_mhz"))
             ach = flops_launch / (avg_ms * 1e-3) / 1e12
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": recorded_traffic(dom),
+                    "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
                     "peak_src": ("FP32 FMA lanes x clock" if args.mode == "mixed" else "FP64 FMA rate measured on this pool")
                     + "; achieved counts 5 N log2 N per DFT",
                     "hbm_gbs_algorithmic": bytes_launch / (avg_ms * 1e-3) / 1e9}
