@@ -109,12 +109,16 @@ struct AnalysisProbA : AnalysisProb {
 struct SynthesisProb {
   static constexpr bool kBulkB = true;
   const cx<float>* Y; TcTab tb; int Lb; ColSet cs; cx<float>* Z;
-  // K chunks over ni: the table's run for (m', l-tile) (empty if m' > max l of the tile)
+  // K chunks over ni: the table's run for (m', l-tile); empty if m' > max l of the tile, or
+  // if every |m| of the m-tile exceeds it (Z_{m l m'} is read only for l >= |m|)
   __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& l0, int& kb, int& ke) const {
     mp = bz; mi0 = by * (BM / 2); l0 = bx * BNC;
     const int2 rg = tb.range[mp * tb.ntiles + bx];
+    const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
+    const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
+    const int lhi = min(l0 + BNC, Lb) - 1;
     kb = rg.x * TC_CHUNK_K;
-    ke = (rg.x + rg.y) * TC_CHUNK_K;
+    ke = amin > lhi ? kb : (rg.x + rg.y) * TC_CHUNK_K;
   }
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
     const int mi = mi0 + (r >> 1);
