@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--lam", type=float, default=2.0)
     ap.add_argument("--J0", type=int, default=2)
     ap.add_argument("--mode", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--fp64-tc", action="store_true",
+                    help="with --mode fp64: the contractions on the tensor cores at FP64 accuracy (CRV_F_FP64_TC)")
     ap.add_argument("--unrotated", action="store_true",
                     help="coefficients of the unrotated curvelets (CRV_F_UNROTATED: single-term l = |n| contraction)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -173,6 +175,7 @@ def kind_work(L, lam, J0, el_bytes, w_bytes, unrot=False):
             # single term l = |n|: the volume is written (analysis) or read (synthesis) once
             terms = Lb * Lb * Lb
         add("contract_analysis", vol, 4.0 * terms)
+        add("oz_analysis", vol, 4.0 * terms)
         add("tc_analysis", vol, 4.0 * terms)
         Nh = (Nc + 1) // 2                      # columns n >= 0 (real signals: F_{-m,-n} = conj F_{m,n})
         ring_h = Lb * N * Nh * el_bytes         # ring buffer [b][a][h]
@@ -183,6 +186,7 @@ def kind_work(L, lam, J0, el_bytes, w_bytes, unrot=False):
         add("ring_fwd_a", ring_h + vol, Lb * Nh * fft_flops(N))
         add("beta_quad", 2 * vol, Mc * Nc * (fft_flops(N) + 2 * fft_flops(Q) + 6 * Q))
         add("contract_synthesis", vol, 4.0 * terms)
+        add("oz_synthesis", vol, 4.0 * terms)
         add("tc_synthesis", vol, 4.0 * terms)
     return w
 
@@ -403,6 +407,8 @@ def main():
     build.build()
     L, lam, J0, B = args.L, args.lam, args.J0, args.B
     flags = crv.CRV_F_REAL | (crv.CRV_F_MIXED | crv.CRV_F_W_FP32 if args.mode == "mixed" else 0)
+    if args.mode == "fp64" and args.fp64_tc:
+        flags |= crv.CRV_F_FP64_TC
     unrot_flag = crv.CRV_F_UNROTATED if args.unrotated else 0
     flags |= unrot_flag
     if args.tune:
@@ -524,28 +530,75 @@ def main():
         torch.cuda.synchronize()
         n64 = args.fp64_sample_maps
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        crv.crv_profile_reset()
+        crv.crv_profile_enable((1 << len(kinds)) - 1)
         a.record(stream)
         for i in range(n64):
             crv.crv_analysis(p64.handle, maps[i:i + 1], W64, P64, 1, stream.cuda_stream)
             crv.crv_synthesis(p64.handle, W64, P64, o64, 1, stream.cuda_stream)
         b_.record(stream)
         torch.cuda.synchronize()
+        crv.crv_profile_enable(0)
         ms64 = a.elapsed_time(b_) / n64
+        cc64 = sum(crv.crv_profile_read(kinds.index(k))[1] for k in ("contract_analysis", "contract_synthesis")) / n64
         rec64 = float(torch.linalg.vector_norm(o64[0] - maps[n64 - 1]) / torch.linalg.vector_norm(maps[n64 - 1]))
         if n64 > 1:
             with torch.cuda.stream(stream):
                 crv.crv_analysis(p64.handle, maps[0:1], W64, P64, 1, stream.cuda_stream)
             torch.cuda.synchronize()
         per_scale = {}
+        rings64 = {}
         for j in range(J0, plan.J + 1):
             ref = W64[j]
             per_scale[str(j)] = float(torch.linalg.vector_norm(W[j][:1].double() - ref) / torch.linalg.vector_norm(ref))
+            Lb = plan.Lj[j]
+            rings64[j] = ref[:, sorted({0, Lb // 3, Lb - 1})].clone()
         fp64 = {"maps_per_s": 1000.0 / ms64, "ms_per_map": ms64, "sample_maps": n64,
                 "speedup_mixed_over_fp64": (1000.0 / ms64 and value / world / (1000.0 / ms64)),
                 "roundtrip_rel_l2": rec64, "mixed_vs_fp64_rel_l2_per_scale": per_scale,
                 "mixed_vs_fp64_rel_l2_max": max(per_scale.values())}
         p64.close()
         del W64, P64
+        torch.cuda.empty_cache()
+        if not args.unrotated:
+            # the same map with the contractions on the tensor cores at FP64 accuracy: time per
+            # map, and its coefficients on sampled rings of every scale against the CUDA-core path
+            with torch.cuda.stream(stream):
+                ptc = crv.Plan(L, lam, J0, 0, crv.CRV_F_REAL | crv.CRV_F_FP64_TC, max_batch=1,
+                               stream=stream.cuda_stream)
+                Wtc = ptc.W_tensors(1)
+                Ptc = ptc.Wphi_tensor(1)
+            torch.cuda.synchronize()
+            crv.crv_profile_reset()
+            crv.crv_profile_enable((1 << len(kinds)) - 1)
+            a.record(stream)
+            crv.crv_analysis(ptc.handle, maps[0:1], Wtc, Ptc, 1, stream.cuda_stream)
+            crv.crv_synthesis(ptc.handle, Wtc, Ptc, o64, 1, stream.cuda_stream)
+            b_.record(stream)
+            torch.cuda.synchronize()
+            crv.crv_profile_enable(0)
+            mstc = a.elapsed_time(b_)
+            kind_tc = {}
+            for k, name in enumerate(kinds):
+                n, t = crv.crv_profile_read(k)
+                if n:
+                    kind_tc[name] = t
+            crv.crv_plan_check(ptc.handle)
+            rtc = {}
+            for j in range(J0, plan.J + 1):
+                Lb = plan.Lj[j]
+                got = Wtc[j][:, sorted({0, Lb // 3, Lb - 1})]
+                rtc[str(j)] = float(torch.linalg.vector_norm(got - rings64[j]) / torch.linalg.vector_norm(rings64[j]))
+            fp64["fp64_tc"] = {
+                "ms_per_map": mstc, "speedup_over_fp64_cuda_cores": ms64 / mstc,
+                "contraction_ms": kind_tc.get("oz_analysis", 0.0) + kind_tc.get("oz_synthesis", 0.0),
+                "cuda_core_contraction_ms": cc64,
+                "roundtrip_rel_l2": float(torch.linalg.vector_norm(o64[0] - maps[0]) / torch.linalg.vector_norm(maps[0])),
+                "vs_fp64_cuda_cores_sampled_rings_rel_l2_max": max(rtc.values()),
+                "kernels_ms": kind_tc}
+            ptc.close()
+            del Wtc, Ptc
+        del rings64
 
     # roofline of the dominant kernel kind
     peaks = measured_peaks()
@@ -566,6 +619,14 @@ def main():
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
                     "peak_src": "FP32 FMA lanes x clock" if args.mode == "mixed" else "FP64 FMA rate measured on this pool"}
+        elif dom in ("oz_analysis", "oz_synthesis"):
+            flops_launch = flops_map / per_launch_units
+            peak = peaks["bf16_tflops_sustained"] / 2.0  # TF32 = bf16 / 2 (nominal ratio)
+            ach = flops_launch / (avg_ms * 1e-3) / 1e12
+            roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
+                    "peak_src": f"{peaks['src']} bf16 sustained / 2 (tf32); achieved counts FP64-accurate flops, "
+                                "28 TF32 slice products each (slicing included)"}
         elif dom in ("tc_analysis", "tc_synthesis"):
             flops_launch = flops_map / per_launch_units
             peak = peaks["bf16_tflops_sustained"] / 2.0  # TF32 = bf16 / 2 (nominal ratio)

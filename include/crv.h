@@ -72,6 +72,14 @@ enum {
   CRV_F_TUNE = 16,   /* autotune at creation: time a batch of zero maps for each number of
                        concurrent map workers (1, 2, 4, 8 up to max_batch) and ring-chunk size
                        (64 MB, 256 MB) and keep the fastest (crv_plan_tuning reports it) */
+  CRV_F_FP64_TC = 32, /* plain FP64 plans only: the two Delta contractions (Eqs. inverse_Fmnmp and
+                         flml) run on the TF32 tensor cores with FP64 accuracy, by error-free
+                         splitting: each operand row is scaled by a power of two and cut into
+                         seven integer slices of 7 bits (6 bits when a K range exceeds 1024:
+                         complex signals above L = 512), slice products of one level accumulate
+                         exactly in FP32, and the levels are added in FP64. Sliced Delta Psi tables per scale are built at creation
+                         (about 7x the size of the FP32 ones); the per-map A operands are sliced
+                         into a 4 GB buffer in passes over m' (CRV_FP64_TC_A_GB sets its size) */
   CRV_F_UNROTATED = 8 /* W_j are the coefficients of the unrotated curvelets s-psi~^(j) (Sec. III-A-1),
                          i.e. W~(rho) with W(rho) = W~(rho rho*), rho* = (0, vartheta^j, 0) (Eq.
                          rotateWigner). Their Wigner coefficients vanish unless |n| = l (Eq.

@@ -14,7 +14,7 @@ import os
 
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
-    "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CRV_F_TUNE", "CrvError",
+    "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CRV_F_TUNE", "CRV_F_FP64_TC", "CrvError",
     "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_tuning", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
     "crv_synthesis", "crv_analysis_lm", "crv_synthesis_lm", "crv_rotate_wigner", "crv_rotate_wigner_adjoint", "crv_delta_table_noalloc", "CRV_NOALLOC_MAX_L", "crv_last_error", "crv_status_string",
@@ -24,7 +24,7 @@ __all__ = [
 
 CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED = range(6)
 CRV_NRULE_CURVELET = 0
-CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED, CRV_F_TUNE = 1, 2, 4, 8, 16
+CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED, CRV_F_TUNE, CRV_F_FP64_TC = 1, 2, 4, 8, 16, 32
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None

@@ -76,7 +76,7 @@ __host__ __device__ __forceinline__ double parity_sign(int k) { return (k & 1) ?
 // Kernel kinds, for launch accounting and optional event timing.
 enum KernelKind {
   K_DELTA = 0, K_SHT_CONTRACT, K_SHT_ROWS, K_BETA_SYNTH, K_BETA_QUAD, K_RING_INV_N, K_RING_INV_M,
-  K_RING_FWD_G, K_RING_FWD_A, K_CONTRACT_A, K_CONTRACT_S, K_TC_A, K_TC_S, K_MISC, K_SHT_BETA, K_ROTATE, K_NKINDS
+  K_RING_FWD_G, K_RING_FWD_A, K_CONTRACT_A, K_CONTRACT_S, K_TC_A, K_TC_S, K_MISC, K_SHT_BETA, K_ROTATE, K_OZ_A, K_OZ_S, K_NKINDS
 };
 const char* kind_name(int k);
 

@@ -1,6 +1,6 @@
 // libcrv host side: plan construction, per-scale pipelines and the C ABI of
-// include/crv.h. Device work lives in delta.cu, transforms.cuh, contract.cuh and
-// tc_contract.cu.
+// include/crv.h. Device work lives in delta.cu, transforms.cuh, contract.cuh,
+// tc_contract.cu, tc_ozaki.cu and rotate.cu.
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -18,6 +18,7 @@
 #include "contract.cuh"
 #include "rotate.cuh"
 #include "tc_contract.cuh"
+#include "tc_ozaki.cuh"
 
 namespace crv {
 
@@ -30,7 +31,8 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 static const char* kKindNames[K_NKINDS] = {"delta", "sht_contract", "sht_rows", "beta_synth", "beta_quad",
                                            "ring_inv_n", "ring_inv_m", "ring_fwd_g", "ring_fwd_a",
                                            "contract_analysis", "contract_synthesis", "tc_analysis",
-                                           "tc_synthesis", "misc", "sht_beta", "rotate"};
+                                           "tc_synthesis", "misc", "sht_beta", "rotate",
+                                           "oz_analysis", "oz_synthesis"};
 const char* kind_name(int k) { return (k >= 0 && k < K_NKINDS) ? kKindNames[k] : "?"; }
 struct ProfState {
   std::mutex mu;
@@ -268,6 +270,24 @@ struct crv_plan_s {
   int* d_err = nullptr;   // [0]: set by kernels whose bounded waits gave up; [1]: tile counter of the tensor-core engine
   size_t vol_bytes = 0, ring_bytes = 0;
   long long a_chunks = 0;  // chunks of the per-map A tables of the analysis (largest scale)
+  // FP64 tensor-core contractions (CRV_F_FP64_TC): per scale the sliced B tables of the two
+  // contractions, and the layout of the per-map A tables with the passes over m' that keep
+  // one pass's A table within oz_cap chunks (one buffer per instance)
+  bool use_oz = false;
+  struct OzA {
+    const long long* base = nullptr;
+    const int2* range = nullptr;
+    int ntiles = 0;
+    std::vector<long long> cum;  // chunk offset of m' (its first tile)
+    std::vector<int> cuts;       // pass boundaries over m': cuts[i] .. cuts[i + 1]
+  };
+  std::vector<OzTab> ozBA, ozBS;
+  std::vector<OzA> ozAA, ozAS;
+  long long oz_cap = 0;  // chunks of the A buffer
+  int oz_bits = 7;       // digit width: 7 while every K range is <= 1024, else 6
+  int oz_mp_cap = 0;     // largest number of m' in a pass (rows of the exponent buffer)
+  float* oz_av = nullptr;
+  int* oz_ae = nullptr;
   std::shared_ptr<TableSet> tabs;  // read-only tables, shared with clones
   std::vector<void*> allocs;       // this instance's workspace
   size_t bytes = 0;
@@ -335,6 +355,22 @@ struct crv_plan_s {
     return c;
   }
 };
+
+// The A table of pass [cuts[i], cuts[i + 1]) of a per-map A layout, in the plan's buffer.
+static OzTab oz_pass(const crv_plan_s* p, const crv_plan_s::OzA& a, int i) {
+  OzTab t;
+  t.mp0 = a.cuts[i];
+  t.mp1 = a.cuts[i + 1];
+  t.v = p->oz_av;
+  t.e = p->oz_ae;
+  t.base = a.base + (size_t)t.mp0 * a.ntiles;
+  t.range = a.range + (size_t)t.mp0 * a.ntiles;
+  t.ntiles = a.ntiles;
+  t.rows = a.ntiles * OZ_AROWS;
+  t.c0 = a.cum[t.mp0];
+  t.bits = p->oz_bits;
+  return t;
+}
 
 template <class T> static const DftTab<T>& dft_of(const FftSet& s);
 template <> const DftTab<double>& dft_of<double>(const FftSet& s) { return s.d; }
@@ -681,6 +717,16 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
   cx<T>* Xb = (cx<T>*)p->wXb;
   cx<T>* R = (cx<T>*)p->wR;
   bool used_tc = false;
+  if constexpr (sizeof(T) == 8) {
+    if (p->use_oz) {
+      const crv_plan_s::OzA& a = p->ozAA[j];
+      for (int i = 0; i + 1 < (int)a.cuts.size(); ++i)
+        if (!oz_analysis(p->dQ, p->L, flm, oz_pass(p, a, i), p->ozBA[j], Lb, cs, (cx<double>*)X, p->d_err,
+                         p->d_err + 1, st))
+          return false;
+      used_tc = true;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     if (p->use_tc) {
       if (!tc_analysis(p->dQ32, p->L, p->wflm32, p->tabA[j], Lb, cs, (cx<float>*)X, p->d_err, p->d_err + 1, st,
@@ -771,6 +817,18 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
     count_launch();  // the timer counts the first of its two launches
     kt.done();
     return launch_ok("unrot_reduce_kernel");
+  }
+  if constexpr (sizeof(T) == 8) {
+    // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
+    if (p->use_oz) {
+      const crv_plan_s::OzA& a = p->ozAS[j];
+      cx<double>* Z = (cx<double>*)p->wXb;
+      for (int i = 0; i + 1 < (int)a.cuts.size(); ++i)
+        if (!oz_synthesis_products((const cx<double>*)Y, oz_pass(p, a, i), p->ozBS[j], Lb, cs, Z, p->d_err,
+                                   p->d_err + 1, st))
+          return false;
+      return oz_synthesis_reduce(p->dQ, p->L, Z, Lb, cs, flm, st);
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // Xb is consumed by the beta quadrature, so its buffer holds the per-m' products
@@ -964,6 +1022,104 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
   return CRV_OK;
 }
 
+// Sliced tables of the FP64 tensor-core contractions (tc_ozaki.cuh): the B tables of every
+// scale, filled here, and the layout of the per-map A tables with the passes over m'.
+static int build_oz_tables(crv_plan_s* p, cudaStream_t st) {
+  int stt = CRV_OK;
+  p->ozBA.assign(p->J + 1, OzTab());
+  p->ozBS.assign(p->J + 1, OzTab());
+  p->ozAA.assign(p->J + 1, crv_plan_s::OzA());
+  p->ozAS.assign(p->J + 1, crv_plan_s::OzA());
+  auto layout = [](const std::vector<int2>& range, std::vector<long long>& base) {
+    base.resize(range.size());
+    long long total = 0;
+    for (size_t i = 0; i < range.size(); ++i) {
+      base[i] = total - range[i].x;
+      total += range[i].y;
+    }
+    return total;
+  };
+  // A buffer: CRV_FP64_TC_A_GB (default 4) GB, at least the largest single m'
+  double gb = 4.0;
+  if (const char* e = getenv("CRV_FP64_TC_A_GB")) gb = std::max(0.01, atof(e));
+  long long cap = (long long)(gb * (double)(1ull << 30) / ((double)OZ_ACHUNK * sizeof(float)));
+  int kmax = 0;  // longest K range: l < L_j (analysis), the n columns (synthesis)
+  for (int j = p->J0; j <= p->J; ++j) kmax = std::max(kmax, std::max(p->Lj[j], p->colset(p->Lj[j]).Nc));
+  p->oz_bits = kmax <= 1024 ? 7 : 6;
+  if (const char* e = getenv("CRV_FP64_TC_BITS"))  // 6 forces the narrower digits (never wider)
+    if (atoi(e) == 6) p->oz_bits = 6;
+  for (int j = p->J0; j <= p->J && stt == CRV_OK; ++j) {
+    const int Lb = p->Lj[j];
+    const ColSet cs = p->colset(Lb);
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<int2> range;
+      std::vector<long long> base;
+      int ntiles = 0;
+      if (dir == 0) oz_ranges_b_analysis(Lb, cs, range, ntiles);
+      else oz_ranges_b_synthesis(Lb, cs, range, ntiles);
+      const long long total = layout(range, base);
+      OzTab t;
+      t.v = p->talloc<float>((size_t)std::max<long long>(total, 1) * OZ_BCHUNK, &stt);
+      t.e = p->talloc<int>((size_t)Lb * ntiles * OZ_BROWS, &stt);
+      long long* dbase = p->talloc<long long>(base.size(), &stt);
+      int2* drange = p->talloc<int2>(range.size(), &stt);
+      if (stt != CRV_OK) return stt;
+      cudaMemcpy(dbase, base.data(), base.size() * sizeof(long long), cudaMemcpyHostToDevice);
+      cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
+      t.base = dbase; t.range = drange; t.ntiles = ntiles; t.rows = ntiles * OZ_BROWS;
+      t.mp0 = 0; t.mp1 = Lb; t.c0 = 0; t.bits = p->oz_bits;
+      const bool ok = dir == 0 ? oz_fill_b_analysis(p->dQ, p->L, p->dpsi[j], Lb, cs, t, st)
+                               : oz_fill_b_synthesis(p->dQ, p->L, p->dpsi[j], Lb, cs, t, st);
+      if (!ok) return CRV_ECUDA;
+      (dir == 0 ? p->ozBA : p->ozBS)[j] = t;
+      // A layout
+      crv_plan_s::OzA& a = (dir == 0 ? p->ozAA : p->ozAS)[j];
+      std::vector<int2> ar;
+      std::vector<long long> ab;
+      if (dir == 0) oz_ranges_a_analysis(Lb, cs, ar, a.ntiles);
+      else oz_ranges_a_synthesis(Lb, cs, ar, a.ntiles);
+      layout(ar, ab);
+      a.cum.assign(Lb + 1, 0);
+      for (int mp = 0; mp < Lb; ++mp) {
+        long long c = 0;
+        for (int t2 = 0; t2 < a.ntiles; ++t2) c += ar[(size_t)mp * a.ntiles + t2].y;
+        a.cum[mp + 1] = a.cum[mp] + c;
+        cap = std::max(cap, c);
+      }
+      long long* dab = p->talloc<long long>(ab.size(), &stt);
+      int2* dar = p->talloc<int2>(ar.size(), &stt);
+      if (stt != CRV_OK) return stt;
+      cudaMemcpy(dab, ab.data(), ab.size() * sizeof(long long), cudaMemcpyHostToDevice);
+      cudaMemcpy(dar, ar.data(), ar.size() * sizeof(int2), cudaMemcpyHostToDevice);
+      a.base = dab;
+      a.range = dar;
+    }
+  }
+  // passes: consecutive m' whose A chunks fit in the buffer
+  long long used = 0;
+  int mpmax = 0;
+  for (int j = p->J0; j <= p->J; ++j)
+    for (crv_plan_s::OzA* a : {&p->ozAA[j], &p->ozAS[j]}) {
+      const int Lb = (int)a->cum.size() - 1;
+      a->cuts.assign(1, 0);
+      int mp0 = 0;
+      for (int mp = 0; mp < Lb; ++mp)
+        if (a->cum[mp + 1] - a->cum[mp0] > cap) {
+          a->cuts.push_back(mp);
+          mpmax = std::max(mpmax, mp - mp0);
+          used = std::max(used, a->cum[mp] - a->cum[mp0]);
+          mp0 = mp;
+        }
+      a->cuts.push_back(Lb);
+      mpmax = std::max(mpmax, Lb - mp0);
+      used = std::max(used, a->cum[Lb] - a->cum[mp0]);
+    }
+  p->oz_cap = used;
+  p->oz_mp_cap = mpmax;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(CRV_ECUDA, "FP64 tensor-core table build failed");
+  return CRV_OK;
+}
+
 // Per-instance workspace of a plan whose tables exist: f_lm buffers, SHT rows, the (m, n, m')
 // volumes, the ring buffer, the error flag and the per-map A tables of the tensor-core analysis.
 static int alloc_workspace(crv_plan_s* p) {
@@ -988,6 +1144,13 @@ static int alloc_workspace(crv_plan_s* p) {
     p->ring_bytes = std::max(one, std::min((size_t)L * one, (size_t)256 << 20));
   }
   p->wR = p->dalloc<unsigned char>(p->ring_bytes, &stt);
+  if (p->use_oz && stt == CRV_OK) {
+    int rows = 0;
+    for (const auto& a : p->ozAA) rows = std::max(rows, a.ntiles * OZ_AROWS);
+    for (const auto& a : p->ozAS) rows = std::max(rows, a.ntiles * OZ_AROWS);
+    p->oz_av = p->dalloc<float>((size_t)std::max<long long>(p->oz_cap, 1) * OZ_ACHUNK, &stt);
+    p->oz_ae = p->dalloc<int>((size_t)std::max(p->oz_mp_cap, 1) * std::max(rows, 1), &stt);
+  }
   if (p->use_tc && stt == CRV_OK) {
     const size_t na = (size_t)std::max<long long>(p->a_chunks, 1) * TC_ACHUNK_FLOATS;
     float* ahi = p->dalloc<float>(na, &stt);
@@ -1017,6 +1180,8 @@ static crv_plan_s* clone_instance(const crv_plan_s* src, int* status) {
   p->wX = p->wXb = p->wR = nullptr;
   p->d_err = nullptr;
   for (auto& t : p->tabAA) { t.hi = nullptr; t.lo = nullptr; }
+  p->oz_av = nullptr;
+  p->oz_ae = nullptr;
   *status = alloc_workspace(p);
   if (*status != CRV_OK) { delete p; return nullptr; }
   return p;
@@ -1161,7 +1326,9 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
   if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");
   if (nrule != CRV_NRULE_CURVELET) return fail(CRV_EINVAL, "unknown nrule");
-  if (flags & ~31u) return fail(CRV_EINVAL, "unknown flag bits");
+  if (flags & ~63u) return fail(CRV_EINVAL, "unknown flag bits");
+  if ((flags & CRV_F_FP64_TC) && (flags & (CRV_F_MIXED | CRV_F_UNROTATED)))
+    return fail(CRV_EINVAL, "CRV_F_FP64_TC is a form of the plain FP64 rotated path (no CRV_F_MIXED, CRV_F_UNROTATED)");
   if ((flags & CRV_F_REAL) && spin != 0) return fail(CRV_EINVAL, "CRV_F_REAL requires spin 0");
   if (max_batch < 1) return fail(CRV_EINVAL, "max_batch must be >= 1");
   int J = 0;
@@ -1181,6 +1348,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->L = L; p->lambda = lambda; p->J0 = J0; p->J = J; p->spin = spin; p->flags = flags; p->max_batch = max_batch;
   p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
   p->unrot = flags & CRV_F_UNROTATED;
+  p->use_oz = flags & CRV_F_FP64_TC;
   p->Lphi = std::max(1, ceil_pow(lambda, J0));
   p->Lphi = std::min(p->Lphi, L);
   p->Lj.assign(J + 1, 0);
@@ -1314,6 +1482,10 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   }
   if (p->use_tc) {
     const int rc = build_tc_tables(p, st);
+    if (rc != CRV_OK) { delete p; return rc; }
+  }
+  if (p->use_oz) {
+    const int rc = build_oz_tables(p, st);
     if (rc != CRV_OK) { delete p; return rc; }
   }
   stt = alloc_workspace(p);

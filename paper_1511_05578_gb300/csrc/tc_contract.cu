@@ -192,6 +192,17 @@ __global__ void __launch_bounds__(256) synth_reduce_kernel(const float* __restri
   f = neg ? f - acc : f + acc;
 }
 
+// Self-test of the error path of the bounded waits: one thread waits on an mbarrier that
+// nothing arrives at, with a limit of `limit` polls; the wait gives up and sets *err. No
+// other thread, copy or MMA is involved, so nothing is left in flight.
+__global__ void bounded_wait_probe_kernel(int* err, long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(&bar, 0u, err, limit);
+}
+
 // Four values as TF32 hi = rna(x) and lo = rna(x - hi) at float offset o of the two tables.
 __device__ __forceinline__ void put_split4(float* hi, float* lo, size_t o, const float* x) {
   uint32_t h[4], l[4];

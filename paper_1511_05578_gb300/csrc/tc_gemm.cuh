@@ -617,17 +617,6 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
   }
 }
 
-// Self-test of the error path of the bounded waits: one thread waits on an mbarrier that
-// nothing arrives at, with a limit of `limit` polls; the wait gives up and sets *err. No
-// other thread, copy or MMA is involved, so nothing is left in flight.
-__global__ void bounded_wait_probe_kernel(int* err, long limit) {
-  __shared__ uint64_t bar;
-  if (threadIdx.x != 0) return;
-  mbar_init(&bar, 1);
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  mbar_wait(&bar, 0u, err, limit);
-}
-
 }  // namespace tc
 
 template <class Prob, int BN>

@@ -104,6 +104,14 @@ def test_L1024_fp64_sampled_rings_and_reconstruction():
     _full_case(1024, 2.0, 2, crv.CRV_F_REAL, 2000, 1e-10, 1e-10, 1e-12, 2, synth_scales=[2, 9, 10])
 
 
+def test_L1024_fp64_tc_sampled_rings_and_reconstruction():
+    """Plain FP64 with the contractions on the tensor cores (CRV_F_FP64_TC, 7-bit digits) at
+    the benchmark's map shape (L=1024, lambda=2, J0=2, seed 2000): the plain path's bars,
+    1e-10 per ring and per scale, 1e-12 round trip."""
+    _full_case(1024, 2.0, 2, crv.CRV_F_REAL | crv.CRV_F_FP64_TC, 2000, 1e-10, 1e-10, 1e-12, 2,
+               synth_scales=[2, 9, 10])
+
+
 def test_L1024_mixed_sampled_rings_and_reconstruction():
     """The benchmark's map shape: L=1024, lambda=2, J0=2, split-FP32 contraction,
     FP32 DFTs and W (seed 2000): 1e-5 relative L2 per ring, per scale and round trip."""
