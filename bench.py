@@ -625,8 +625,8 @@ def main():
             ach = flops_launch / (avg_ms * 1e-3) / 1e12
             roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": recorded_traffic(dom, twl),
-                    "peak_src": f"{peaks['src']} bf16 sustained / 2 (tf32); achieved counts FP64-accurate flops, "
-                                "28 TF32 slice products each (slicing included)"}
+                    "peak_src": f"{peaks['src']} bf16 sustained / 2 (tf32); achieved counts FP64-accurate flops "
+                                "(each one 28 TF32 slice products; slicing included)"}
         elif dom in ("tc_analysis", "tc_synthesis"):
             flops_launch = flops_map / per_launch_units
             peak = peaks["bf16_tflops_sustained"] / 2.0  # TF32 = bf16 / 2 (nominal ratio)
@@ -661,7 +661,7 @@ def main():
         for k, (bts, fl) in work.items():
             if k not in kind_ms:
                 continue
-            if k.startswith("tc_"):
+            if k.startswith(("tc_", "oz_")):  # tensor-core contractions: the TF32 pipe
                 pk = peaks["bf16_tflops_sustained"] / 2.0 * 1e12
             elif args.mode == "mixed":
                 pk = fp32_alu_peak_tflops(sm) * 1e12

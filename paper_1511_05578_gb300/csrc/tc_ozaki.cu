@@ -10,14 +10,15 @@
 // Both operands are sliced into tables (B once per plan, A per map and per pass over a range
 // of m') in the layout of an engine stage, and both come into shared memory by bulk copies.
 //
-// Engine: persistent, one CTA of 7 warps per SM, tiles taken in order from a global counter.
+// Engine: persistent, one CTA of 11 warps per SM, tiles taken in order from a global counter.
 //   warp 0 (one lane)  schedules tiles into a ring of four slots;
 //   warp 1 (one lane)  bulk-copies the A and B chunks of a K step into one of two stages;
 //   warp 2 (one lane)  issues, per K step of 8, the OZ_S (OZ_S + 1) / 2 slice products
 //                      s + t < OZ_S into five TMEM accumulators of 96 columns (levels 0-3,
 //                      and 4 and above together) and commits to the stage's empty barrier;
-//   warps 3-6          drain the accumulators, add them in double-float, scale by the row
-//                      and column exponents and store FP64 results.
+//   warps 3-10         drain the accumulators (two warps per TMEM lane quarter, half of the
+//                      columns each), add them in double-float, scale by the row and
+//                      column exponents and store FP64 results (one FP64 add per value).
 // Every mbarrier wait is bounded and sets the plan's error flag when it gives up; the other
 // roles then stop in turn, copies in flight are waited for and the MMA lane waits for its
 // MMAs before TMEM is released.
@@ -46,7 +47,8 @@ constexpr int BN = OZ_BROWS;
 constexpr int ASL_BYTES = OZ_ASLICE * 4, BSL_BYTES = OZ_BSLICE * 4;  // one slice of a chunk
 constexpr int A_BYTES = OZ_ACHUNK * 4, B_BYTES = OZ_BCHUNK * 4;      // all slices of a chunk
 constexpr int STAGES = 2, STAGE_BYTES = A_BYTES + B_BYTES, RING = 4;
-constexpr int THREADS = 7 * 32;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each half of the columns
+constexpr int THREADS = (3 + EPI_WARPS) * 32;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 512;
 constexpr uint32_t TMEM_COLS = 512;
 // instruction descriptor: D f32, A/B tf32, K-major A and B, N = 96, M = 128
@@ -55,32 +57,67 @@ constexpr uint32_t IDESC =
 static_assert(OZ_ACCS * BN <= (int)TMEM_COLS, "accumulators fit in TMEM");
 static_assert(SMEM_BYTES <= 227 * 1024, "two stages fit in shared memory");
 static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "valid MMA N for M = 128");
+static_assert((BN / 2) % 16 == 0, "each epilogue warp drains whole 16-column loads");
 static_assert(OZ_K == 16 && OZ_AROWS % 8 == 0 && OZ_BROWS % 8 == 0, "stage layout");
 
 // ---------------------------------------------------------------------------
 // Slicing
 // ---------------------------------------------------------------------------
-// Row exponent: E with max |x| < 2^E (0 for a zero row).
-__device__ __forceinline__ int row_exp(double amax) { return amax > 0.0 ? ilogb(amax) + 1 : 0; }
-
-// The OZ_S slices d_k 2^(-bk) of x for the row scale 2^E and b-bit digits,
-// x ~ 2^(E - b + 1) sum_k d_k 2^(-bk), d_k = round(s_k), s_0 = x 2^(b - 1 - E),
-// s_{k+1} = 2^b (s_k - d_k): |s_k| <= 2^(b-1) so |d_k| <= 2^(b-1), every step exact in FP64.
-__device__ __forceinline__ void slice(double x, int E, int b, float* d) {
-  double s = scalbn(x, b - 1 - E);
-  const double radix = (double)(1 << b);
-#pragma unroll
-  for (int k = 0; k < OZ_S; ++k) {
-    const double dk = rint(s);
-    d[k] = (float)dk * __int_as_float((127 - b * k) << 23);
-    s = (s - dk) * radix;
-  }
+// Row exponent from the largest |x| as a bit pattern (non-negative doubles order like their
+// bits): E with max |x| < 2^E; 0 for a row of zeros and subnormals, which slice to zero.
+__device__ __forceinline__ int row_exp(unsigned long long amax_bits) {
+  const int ef = (int)(amax_bits >> 52);
+  return ef == 0 ? 0 : ef - 1022;
+}
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// 2^e as a double (e within the normal range; scalbn outside it).
+// The OZ_S slices d_k 2^(-bk) of x for the row scale 2^E and b-bit digits, with
+// x ~ 2^(E - b + 1) sum_k d_k 2^(-bk), in integer arithmetic: T = round(|x| 2^(OZ_S b - 1 - E))
+// from the 53-bit mantissa (|T| <= 2^(OZ_S b - 1)), signed, then balanced base-2^b digits from
+// the least significant up, d_k in [-2^(b-1), 2^(b-1)), the top digit taking the rest
+// (|d_0| <= 2^(b-1)). One rounding, at 2^(-OZ_S b + 1) of the row scale.
+__device__ __forceinline__ void slice(double x, int E, int b, float* d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((u >> 52) & 0x7ff);
+  long long T = 0;
+  if (ef != 0) {
+    const unsigned long long m = (u & 0xfffffffffffffull) | (1ull << 52);  // |x| = m 2^(ef - 1075)
+    const int rs = 1076 + E - OZ_S * b - ef;  // >= 54 - OZ_S b (5 for b = 7) because |x| < 2^E
+    if (rs < 63) T = (long long)((m + (1ull << (rs - 1))) >> rs);
+    if (u >> 63) T = -T;
+  }
+  const long long mask = (1ll << b) - 1, half = 1ll << (b - 1);
+#pragma unroll
+  for (int k = OZ_S - 1; k >= 1; --k) {
+    long long r = T & mask;
+    if (r >= half) r -= mask + 1;
+    d[k] = (float)(int)r * __int_as_float((127 - b * k) << 23);
+    T = (T - r) >> b;
+  }
+  d[0] = (float)(int)T;
+}
+
+// FP32 -> FP64 by the bit patterns (exact for normal values; zeros and subnormals, which the
+// accumulators do not produce above 2^-126 of a result, give 0), so that the epilogue spends
+// no FP64 instruction on it.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if (ex == 0) return 0.0;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ex + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// x 2^e by the exponent field (scalbn when the result leaves the normal range).
 __device__ __forceinline__ double scale2(double x, int e) {
-  if (e > -1022 && e < 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
-  return scalbn(x, e);
+  const long long u = __double_as_longlong(x);
+  const int ex = (int)((u >> 52) & 0x7ff);
+  if (ex == 0) return x;
+  const int ne = ex + e;
+  if (ne <= 0 || ne >= 2047) return scalbn(x, e);
+  return __longlong_as_double(u + ((long long)e << 52));
 }
 
 // Four consecutive K values of one row, sliced into the OZ_S slices of the chunk at `chunk`
@@ -106,9 +143,9 @@ __global__ void __launch_bounds__(128) fill_kernel(V val, OzTab t) {
   const size_t idx = (size_t)mpl * t.ntiles + tile;
   const int2 rg = t.range[idx];
   const int row = tile * ROWS + r;
-  double amax = 0.0;
+  unsigned long long amax = 0;
   for (int kc = rg.x; kc < rg.x + rg.y; ++kc)
-    for (int i = 0; i < OZ_K; ++i) amax = fmax(amax, fabs(val.at(mp, row, kc * OZ_K + i)));
+    for (int i = 0; i < OZ_K; ++i) amax = max(amax, abs_bits(val.at(mp, row, kc * OZ_K + i)));
   const int E = row_exp(amax);
   t.e[(size_t)mpl * t.rows + row] = E;
   constexpr int CH = OZ_S * ROWS * OZ_K;
@@ -287,10 +324,10 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(Prob pb, int gx, in
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, EPI_WARPS);
     for (int i = 0; i < RING; ++i) {
       mbar_init(&tr_full[i], 1);
-      mbar_init(&tr_empty[i], 6);  // copy lane, MMA lane, four epilogue warps
+      mbar_init(&tr_empty[i], 2 + EPI_WARPS);  // copy lane, MMA lane, epilogue warps
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -394,8 +431,9 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(Prob pb, int gx, in
       if (issued) mma_drain(drain, err);
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns of half (w - 3) / 4 ----
     const int lq = warp & 3, r = lq * 32 + lane;
+    const int cbeg = ((warp - 3) / 4) * (BN / 2), cend = cbeg + BN / 2;
     for (uint32_t j = 0;; ++j) {
       const int sl = j % RING;
       if (!warp_wait(&tr_full[sl], (j / RING) & 1u, err)) break;
@@ -409,7 +447,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(Prob pb, int gx, in
       fence_after();
       const int er = ti.nch > 0 ? pb.ea(ti, r) : 0;
       const int eoff = 2 * (pb.ta.bits - 1);  // x = 2^(E - b + 1) sum_k d_k 2^(-bk) for both operands
-      for (int cc = 0; cc < BN; cc += 16) {
+      for (int cc = cbeg; cc < cend; cc += 16) {
         double v[16];
         if (ti.nch > 0) {
           float a[OZ_ACCS][16];
@@ -428,7 +466,7 @@ __global__ void __launch_bounds__(THREADS, 1) oz_gemm_kernel(Prob pb, int gx, in
             h = h2;
 #pragma unroll
             for (int g = 3; g < OZ_ACCS; ++g) lo += a[g][i];
-            v[i] = scale2((double)h + (double)lo, er + pb.eb(ti, cc + i) - eoff);
+            v[i] = scale2(f2d(h) + f2d(lo), er + pb.eb(ti, cc + i) - eoff);
           }
         } else {
 #pragma unroll
