@@ -29,6 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PROF_MAPS = 2  # maps of the separate per-kind timing pass
 METRIC = "maps/s analysis+synthesis at L=1024, mixed vs FP64 (err<=1e-5); p50/p99 ms"
 
 
@@ -55,7 +56,9 @@ def parse():
     ap.add_argument("--batch-calls", action="store_true",
                     help="one analysis and one synthesis call per step for all B maps (the plan's map workers run "
                          "them concurrently; small band limits), instead of one call per map")
-    ap.add_argument("--maps-per-call", type=int, default=1, help="maps per analysis/synthesis call (a divisor of B)")
+    ap.add_argument("--maps-per-call", type=int, default=2,
+                    help="maps per analysis/synthesis call (a divisor of B); with 2 or more the plan runs two "
+                         "maps at once on two instances where memory allows")
     ap.add_argument("--tune", action="store_true", help="create the plan with CRV_F_TUNE (autotuned workers and ring chunks)")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving leg (Poisson arrivals; 0 = skip)")
@@ -376,9 +379,10 @@ def serving_leg(args):
 def config_dict(args):
     return {"workload": f"curvelet analysis+synthesis, {args.B} real spin-0 maps, L={args.L}, lambda={args.lam:g}, "
                         f"J0={args.J0}, {'mixed precision (split-FP32 contraction, FP32 FFT/W)' if args.mode == 'mixed' else 'plain FP64'}"
+                        + (", FP64-accurate contractions on tensor cores" if args.mode == "fp64" and args.fp64_tc else "")
                         + (", unrotated curvelets (O(L^3) single-term contraction)" if args.unrotated else ""),
             "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
-            "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.B if args.batch_calls else max(1, args.maps_per_call),
+            "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.maps_per_call if not args.batch_calls else args.B,
             "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)" if args.L >= 1024 else
                   "inputs of a step smaller than L2 at this band limit"}
 
@@ -414,6 +418,8 @@ def main():
     if args.tune:
         flags |= crv.CRV_F_TUNE
     nb = B if args.batch_calls else max(1, args.maps_per_call)  # maps per call
+    nb = math.gcd(B, min(nb, B))  # a divisor of B (B = 1: one map per call)
+    args.maps_per_call = nb
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         plan = crv.Plan(L, lam, J0, 0, flags, max_batch=nb, stream=stream.cuda_stream)
@@ -445,8 +451,6 @@ def main():
     recon = float(torch.linalg.vector_norm(out[-1] - maps[-1]) / torch.linalg.vector_norm(maps[-1]))
 
     kinds = crv.crv_profile_kinds()
-    crv.crv_profile_reset()
-    crv.crv_profile_enable((1 << len(kinds)) - 1)
     l0 = crv.crv_launch_count()
     clocks = ClockSampler(local)
     barrier()
@@ -472,15 +476,25 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = crv.crv_launch_count() - l0
-    crv.crv_profile_enable(0)
     ms_total = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b_) for a, b_ in per_step]
+    # per-kind device times from a pass of their own after the timed region (no event records
+    # in the timed steps): PROF_MAPS maps, one per call on one plan instance, so that no kernel
+    # shares the GPU with a concurrent map's
+    prof_maps = min(B, PROF_MAPS)
+    crv.crv_profile_reset()
+    crv.crv_profile_enable((1 << len(kinds)) - 1)
+    for b in range(prof_maps):
+        crv.crv_analysis(plan.handle, maps[b:b + 1], W, Wphi, 1, stream.cuda_stream)
+        crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + 1], 1, stream.cuda_stream)
+    torch.cuda.synchronize()
+    crv.crv_profile_enable(0)
     kind_ms = {}
     kind_n = {}
     for k, name in enumerate(kinds):
         n, t = crv.crv_profile_read(k)
         if n:
-            kind_ms[name], kind_n[name] = t, n
+            kind_ms[name], kind_n[name] = t / prof_maps, n / prof_maps  # per map
     t_max = max_over_ranks(ms_total, world, "cuda")
     ms_per_step = t_max / args.steps
     value = whole_job_rate(world, B, args.steps, t_max)
@@ -495,22 +509,22 @@ def main():
     if not args.no_e2e:
         host_in = maps.cpu().pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        dev_in = torch.empty((1, L, 2 * L - 1), dtype=torch.float64, device="cuda")
+        dev_in = torch.empty((nb, L, 2 * L - 1), dtype=torch.float64, device="cuda")
         dev_out = torch.empty_like(dev_in)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for b in range(B):
-                dev_in.copy_(host_in[b:b + 1], non_blocking=True)
-                crv.crv_analysis(plan.handle, dev_in, W, Wphi, 1, stream.cuda_stream)
-                crv.crv_synthesis(plan.handle, W, Wphi, dev_out, 1, stream.cuda_stream)  # one map per call
-                host_out[b:b + 1].copy_(dev_out, non_blocking=True)
+            for b in range(0, B, nb):  # the calls of the timed steps: nb maps per call
+                dev_in.copy_(host_in[b:b + nb], non_blocking=True)
+                crv.crv_analysis(plan.handle, dev_in, W, Wphi, nb, stream.cuda_stream)
+                crv.crv_synthesis(plan.handle, W, Wphi, dev_out, nb, stream.cuda_stream)
+                host_out[b:b + nb].copy_(dev_out, non_blocking=True)
         stream.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        nb = B * L * (2 * L - 1) * 8
-        e2e = {"value": whole_job_rate(world, B, 1, 1000.0 * t_e2e), "unit": "maps/s", "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb}
+        nbytes = B * L * (2 * L - 1) * 8
+        e2e = {"value": whole_job_rate(world, B, 1, 1000.0 * t_e2e), "unit": "maps/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
 
     # plain FP64 GPU path on a sample of maps: the mixed/FP64 speedup, and the per-scale error
     # of the mixed coefficients against the FP64 path's on the same map (the FP64 path matches
@@ -610,7 +624,7 @@ def main():
     roof = None
     if dom:
         avg_ms = kind_ms[dom] / kind_n[dom]
-        per_launch_units = kind_n[dom] / (args.steps * B)  # launches of this kind per map
+        per_launch_units = kind_n[dom]  # launches of this kind per map
         bytes_map, flops_map = work.get(dom, (0.0, 0.0))
         if dom in ("contract_analysis", "contract_synthesis"):
             flops_launch = flops_map / per_launch_units
@@ -647,8 +661,9 @@ def main():
                     + "; achieved counts 5 N log2 N per DFT",
                     "hbm_gbs_algorithmic": bytes_launch / (avg_ms * 1e-3) / 1e9}
         roof["avg_launch_ms"] = avg_ms
-        roof["launches"] = kind_n[dom]
+        roof["launches"] = int(round(kind_n[dom] * prof_maps))
         roof["launches_per_map"] = per_launch_units
+        roof["timing"] = f"CUDA events around each launch, separate pass of {prof_maps} maps, one per call"
     # whole-map roofline: per kernel kind the larger of its algorithmic flops over its pipe's
     # peak and its algorithmic bytes over HBM, summed over the kinds, against the measured time
     # per map
@@ -684,7 +699,7 @@ def main():
         "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_map": roof_map,
         "e2e": e2e,
         "fp64_path": fp64, "step_ms": step_ms,
-        "kernels_ms_per_step": {k: v / args.steps for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
+        "kernels_ms_per_map": {k: v for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1])},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, info = oracle_maps_per_s(L, lam, J0, 20, unrot=args.unrotated)  # ~10-15 s of oracle work on 16 host cores
@@ -704,7 +719,7 @@ def main():
             line["serving"] = {"error": f"{type(err).__name__}: {err}"}
     if args.breakdown and rank == 0:
         for k, v in sorted(kind_ms.items(), key=lambda kv: -kv[1]):
-            sys.stderr.write(f"{k:20s} {v / args.steps:10.2f} ms/step  {kind_n[k] // args.steps:7d} launches/step\n")
+            sys.stderr.write(f"{k:20s} {v:10.2f} ms/map  {kind_n[k]:7.0f} launches/map\n")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if plan.handle is not None:

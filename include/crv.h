@@ -103,8 +103,9 @@ enum {
  *             sharing its tables, each with a workspace and a stream of its own: the B maps of
  *             a call run on up to 4 workers at once (map b on worker b mod K), forked from the
  *             call's stream and joined back into it by events, so calls stay stream-ordered.
- *             The environment variable CRV_WORKER_MAX_GB raises the 1 GB workspace limit
- *             (e.g. two L = 1024 maps at once)
+ *             Above 1 GB the plan holds one worker (two maps at once) when the two workspaces
+ *             fit in a quarter of the device memory. The environment variable
+ *             CRV_WORKER_MAX_GB replaces both rules by one workspace limit for up to 4 workers
  *   stream    CUDA stream used for the table build (Delta recursion)
  * Builds the radial kernels kappa^(j) and scaling function (Sec. II-B), the rotated
  * directional components zeta^(j) (Eq. after directionality_normalisation; with
