@@ -56,7 +56,8 @@ typedef enum crv_status {
   CRV_ENOMEM = 2,        /* device allocation of tables or workspace failed */
   CRV_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
   CRV_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
-  CRV_EUNSUPPORTED = 5   /* valid but not supported by this build (e.g. no GPU) */
+  CRV_EUNSUPPORTED = 5,  /* valid but not supported by this build (e.g. no GPU) */
+  CRV_EGUARD = 6         /* a write went past the end of a plan buffer (CRV_F_GUARD plans) */
 } crv_status;
 
 /* Azimuthal band-limit rule. The curvelet rule is the only one: N_j = L_j and the
@@ -80,6 +81,10 @@ enum {
                          exactly in FP32, and the levels are added in FP64. Sliced Delta Psi tables per scale are built at creation
                          (about 7x the size of the FP32 ones); the per-map A operands are sliced
                          into a 4 GB buffer in passes over m' (CRV_FP64_TC_A_GB sets its size) */
+  CRV_F_GUARD = 64,  /* debugging aid in place of a memory checker: every device buffer of the plan
+                        (tables and workspace, workers included) is followed by a 4 KB guard
+                        region of a known byte pattern, which crv_plan_check_guards compares;
+                        costs one synchronisation per allocation at creation, nothing per call */
   CRV_F_UNROTATED = 8 /* W_j are the coefficients of the unrotated curvelets s-psi~^(j) (Sec. III-A-1),
                          i.e. W~(rho) with W(rho) = W~(rho rho*), rho* = (0, vartheta^j, 0) (Eq.
                          rotateWigner). Their Wigner coefficients vanish unless |n| = l (Eq.
@@ -165,6 +170,18 @@ int crv_plan_check_stream(crv_plan_t plan, void* stream);
  * bounded wait of the library does; the next crv_plan_check then returns CRV_ETIMEOUT.
  * Makes no other device work, leaves nothing in flight; CRV_EINVAL for a bad argument. */
 int crv_debug_bounded_wait(crv_plan_t plan, long polls, void* stream);
+
+/* Guard regions (plans created with CRV_F_GUARD; no counterpart in the paper: a check of this
+ * library's own kernels). crv_plan_check_guards waits for the device and compares every guard
+ * region of the plan (shared tables, workspace, workers' workspaces) with its fill pattern:
+ * CRV_OK if all are intact, CRV_EGUARD if any byte past the end of a buffer was written (*nbad,
+ * if not NULL, gets the number of changed regions; crv_last_error names the first), CRV_EINVAL
+ * for a plan without guards. crv_plan_guard_count gives the number of regions (0 without
+ * guards). crv_debug_poke_guard changes one byte inside region `which` from the host, inside
+ * the allocation, to test the check itself. */
+int crv_plan_check_guards(crv_plan_t plan, int* nbad);
+int crv_plan_guard_count(crv_plan_t plan, int* n);
+int crv_debug_poke_guard(crv_plan_t plan, int which);
 
 /* Host copy of plan tables, for inspection and tests.
  *   crv_plan_kernel:  psi[l][n + L_j - 1] = sPsi^(j)_ln (real, Eq. wav_factorized), l < L_j

@@ -13,7 +13,8 @@ import ctypes
 import os
 
 __all__ = [
-    "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED",
+    "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED", "CRV_EGUARD", "CRV_F_GUARD",
+    "crv_plan_check_guards", "crv_plan_guard_count", "crv_debug_poke_guard",
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CRV_F_TUNE", "CRV_F_FP64_TC", "CrvError",
     "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_tuning", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
@@ -22,9 +23,9 @@ __all__ = [
     "Plan",
 ]
 
-CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED = range(6)
+CRV_OK, CRV_EINVAL, CRV_ENOMEM, CRV_ECUDA, CRV_ETIMEOUT, CRV_EUNSUPPORTED, CRV_EGUARD = range(7)
 CRV_NRULE_CURVELET = 0
-CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED, CRV_F_TUNE, CRV_F_FP64_TC = 1, 2, 4, 8, 16, 32
+CRV_F_REAL, CRV_F_MIXED, CRV_F_W_FP32, CRV_F_UNROTATED, CRV_F_TUNE, CRV_F_FP64_TC, CRV_F_GUARD = 1, 2, 4, 8, 16, 32, 64
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lib = None
@@ -61,6 +62,9 @@ def load():
         "crv_plan_check": (i, [vp]),
         "crv_plan_check_stream": (i, [vp, vp]),
         "crv_debug_bounded_wait": (i, [vp, ctypes.c_long, vp]),
+        "crv_plan_check_guards": (i, [vp, ctypes.POINTER(i)]),
+        "crv_plan_guard_count": (i, [vp, ctypes.POINTER(i)]),
+        "crv_debug_poke_guard": (i, [vp, i]),
         "crv_plan_kernel": (i, [vp, i, ctypes.POINTER(d)]),
         "crv_plan_scaling": (i, [vp, ctypes.POINTER(d)]),
         "crv_plan_delta": (i, [vp, i, ctypes.POINTER(d)]),
@@ -219,6 +223,27 @@ def crv_plan_check_stream(plan, stream=None):
 def crv_debug_bounded_wait(plan, polls, stream=None):
     """Launch the self-test of the bounded-wait error path (see include/crv.h)."""
     _check(load().crv_debug_bounded_wait(plan, int(polls), _stream(stream)))
+
+
+def crv_plan_check_guards(plan):
+    """Compare every guard region of a CRV_F_GUARD plan with its pattern: returns the status
+    (CRV_OK or CRV_EGUARD) and the number of changed regions."""
+    n = ctypes.c_int()
+    st = load().crv_plan_check_guards(plan, ctypes.byref(n))
+    if st not in (CRV_OK, CRV_EGUARD):
+        _check(st)
+    return st, n.value
+
+
+def crv_plan_guard_count(plan):
+    n = ctypes.c_int()
+    _check(load().crv_plan_guard_count(plan, ctypes.byref(n)))
+    return n.value
+
+
+def crv_debug_poke_guard(plan, which):
+    """Change one byte inside guard region `which` (tests the check itself)."""
+    _check(load().crv_debug_poke_guard(plan, int(which)))
 
 
 def crv_plan_kernel(plan, j, out):

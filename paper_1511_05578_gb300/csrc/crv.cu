@@ -221,8 +221,18 @@ struct FftSet {
 // Device allocations of the read-only tables of a plan (Delta, Delta Psi tensor-core
 // tables, FFT tables, kernels): one set per crv_plan_create, shared by the plan and its clones
 // (crv_plan_clone) and freed with the last of them.
+// A guard region (CRV_F_GUARD plans): the kGuardBytes after the end of one device buffer,
+// filled with kGuardByte at allocation and compared by crv_plan_check_guards.
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+struct Guard {
+  unsigned char* p;
+  size_t size;  // the buffer's own size (the guard starts there)
+};
+
 struct TableSet {
   std::vector<void*> allocs;
+  std::vector<Guard> guards;
   size_t bytes = 0;
   TableSet() = default;
   TableSet(const TableSet&) = delete;
@@ -301,21 +311,35 @@ struct crv_plan_s {
   int nworkers = 1;                // workers a call uses (<= 1 + workers.size())
   bool tuned = false;              // nworkers and ring_bytes chosen by the autotuner
 
-  static void* raw_alloc(size_t b, int* status) {
+  bool guard = false;         // CRV_F_GUARD: every buffer followed by a checked guard region
+  std::vector<Guard> guards;  // this instance's workspace guards
+
+  // One device buffer of b bytes; with guards, kGuardBytes more, filled with kGuardByte and
+  // recorded in `gl`.
+  void* raw_alloc(size_t b, int* status, std::vector<Guard>* gl) {
     void* p = nullptr;
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
+    cudaError_t e = cudaMalloc(&p, guard ? b + kGuardBytes : b);
     if (e != cudaSuccess) {
       cudaGetLastError();
       *status = fail(CRV_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
       return nullptr;
+    }
+    if (guard) {
+      unsigned char* g = (unsigned char*)p + b;
+      if (cudaMemset(g, kGuardByte, kGuardBytes) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(p);
+        *status = fail(CRV_ECUDA, "guard region initialisation failed");
+        return nullptr;
+      }
+      gl->push_back(Guard{g, b});
     }
     return p;
   }
   // workspace (per instance)
   template <class P> P* dalloc(size_t n, int* status) {
     if (*status != CRV_OK) return nullptr;
-    void* p = raw_alloc(n * sizeof(P), status);
+    void* p = raw_alloc(n * sizeof(P), status, &guards);
     if (!p) return nullptr;
     allocs.push_back(p);
     bytes += std::max<size_t>(n * sizeof(P), 16);
@@ -324,7 +348,7 @@ struct crv_plan_s {
   // read-only tables (shared)
   template <class P> P* talloc(size_t n, int* status) {
     if (*status != CRV_OK) return nullptr;
-    void* p = raw_alloc(n * sizeof(P), status);
+    void* p = raw_alloc(n * sizeof(P), status, &tabs->guards);
     if (!p) return nullptr;
     tabs->allocs.push_back(p);
     tabs->bytes += std::max<size_t>(n * sizeof(P), 16);
@@ -928,6 +952,7 @@ const char* crv_status_string(int s) {
     case CRV_ECUDA: return "CRV_ECUDA";
     case CRV_ETIMEOUT: return "CRV_ETIMEOUT";
     case CRV_EUNSUPPORTED: return "CRV_EUNSUPPORTED";
+    case CRV_EGUARD: return "CRV_EGUARD";
     default: return "unknown status";
   }
 }
@@ -1168,6 +1193,7 @@ static int alloc_workspace(crv_plan_s* p) {
 static crv_plan_s* clone_instance(const crv_plan_s* src, int* status) {
   auto* p = new crv_plan_s(*src);
   p->allocs.clear();
+  p->guards.clear();
   p->bytes = 0;
   p->workers.clear();
   p->wstreams.clear();
@@ -1326,7 +1352,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   if (J0 < 0) return fail(CRV_EINVAL, "J0 must be >= 0");
   if (std::abs(spin) >= L) return fail(CRV_EINVAL, "|spin| must be < L");
   if (nrule != CRV_NRULE_CURVELET) return fail(CRV_EINVAL, "unknown nrule");
-  if (flags & ~63u) return fail(CRV_EINVAL, "unknown flag bits");
+  if (flags & ~127u) return fail(CRV_EINVAL, "unknown flag bits");
   if ((flags & CRV_F_FP64_TC) && (flags & (CRV_F_MIXED | CRV_F_UNROTATED)))
     return fail(CRV_EINVAL, "CRV_F_FP64_TC is a form of the plain FP64 rotated path (no CRV_F_MIXED, CRV_F_UNROTATED)");
   if ((flags & CRV_F_REAL) && spin != 0) return fail(CRV_EINVAL, "CRV_F_REAL requires spin 0");
@@ -1349,6 +1375,7 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
   p->unrot = flags & CRV_F_UNROTATED;
   p->use_oz = flags & CRV_F_FP64_TC;
+  p->guard = flags & CRV_F_GUARD;
   p->Lphi = std::max(1, ceil_pow(lambda, J0));
   p->Lphi = std::min(p->Lphi, L);
   p->Lj.assign(J + 1, 0);
@@ -1617,6 +1644,59 @@ int crv_plan_check_stream(crv_plan_t p, void* stream) {
     }
   }
   if (any) return fail(CRV_ETIMEOUT, "a bounded device-side wait gave up (results of the affected call are invalid)");
+  return CRV_OK;
+}
+
+// The guard regions of a plan: its tables', its own workspace's and its workers'.
+static std::vector<Guard> all_guards(const crv_plan_s* p) {
+  std::vector<Guard> g = p->tabs->guards;
+  for (size_t w = 0; w <= p->workers.size(); ++w) {
+    const crv_plan_s* q = w == 0 ? p : p->workers[w - 1];
+    g.insert(g.end(), q->guards.begin(), q->guards.end());
+  }
+  return g;
+}
+
+int crv_plan_check_guards(crv_plan_t p, int* nbad) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (nbad) *nbad = 0;
+  if (!p->guard) return fail(CRV_EINVAL, "plan was created without CRV_F_GUARD");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return fail(CRV_ECUDA, cudaGetErrorString(e));
+  const std::vector<Guard> g = all_guards(p);
+  std::vector<unsigned char> h(kGuardBytes);
+  int bad = 0;
+  std::string first;
+  for (size_t i = 0; i < g.size(); ++i) {
+    if (cudaMemcpy(h.data(), g[i].p, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(CRV_ECUDA, "guard region read failed");
+    size_t k = 0;
+    while (k < kGuardBytes && h[k] == kGuardByte) ++k;
+    if (k < kGuardBytes) {
+      if (!bad)
+        first = "guard " + std::to_string(i) + " (after a buffer of " + std::to_string(g[i].size) +
+                " bytes) changed at byte " + std::to_string(k) + " past the end";
+      ++bad;
+    }
+  }
+  if (nbad) *nbad = bad;
+  if (bad) return fail(CRV_EGUARD, std::to_string(bad) + " guard region(s) written: " + first);
+  return CRV_OK;
+}
+
+int crv_debug_poke_guard(crv_plan_t p, int which) {
+  if (!p) return fail(CRV_EINVAL, "plan is NULL");
+  if (!p->guard) return fail(CRV_EINVAL, "plan was created without CRV_F_GUARD");
+  const std::vector<Guard> g = all_guards(p);
+  if (which < 0 || which >= (int)g.size()) return fail(CRV_EINVAL, "no such guard region");
+  if (cudaMemset(g[which].p + kGuardBytes / 2, 0, 1) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+    return fail(CRV_ECUDA, "guard poke failed");
+  return CRV_OK;
+}
+
+int crv_plan_guard_count(crv_plan_t p, int* n) {
+  if (!p || !n) return fail(CRV_EINVAL, "null argument");
+  *n = p->guard ? (int)all_guards(p).size() : 0;
   return CRV_OK;
 }
 

@@ -58,7 +58,7 @@ def test_plan_create_rejects_bad_arguments_without_gpu(libpath):
     assert h.crv_plan_create(ctypes.byref(out), 64, 2.0, 0, 0, 7, 0, 1, None) == crv.CRV_EINVAL
     assert h.crv_plan_create(ctypes.byref(out), 64, 2.0, 0, 0, 0, 0, 0, None) == crv.CRV_EINVAL
     # the FP64 tensor-core contractions are a form of the plain rotated path only
-    for bad in (crv.CRV_F_FP64_TC | crv.CRV_F_MIXED, crv.CRV_F_FP64_TC | crv.CRV_F_UNROTATED, 64):
+    for bad in (crv.CRV_F_FP64_TC | crv.CRV_F_MIXED, crv.CRV_F_FP64_TC | crv.CRV_F_UNROTATED, 128):
         assert h.crv_plan_create(ctypes.byref(out), 16, 2.0, 0, 0, 0, bad, 1, None) == crv.CRV_EINVAL
     assert out.value is None
     assert "must" in crv.crv_last_error() or crv.crv_last_error() != ""
