@@ -108,6 +108,7 @@ struct AnalysisProbA : AnalysisProb {
 
 struct SynthesisProb {
   static constexpr bool kBulkB = true;
+  static constexpr bool kPairLoads = true;
   const cx<float>* Y; TcTab tb; int Lb; ColSet cs; cx<float>* Z;
   // K chunks over ni: the table's run for (m', l-tile); empty if m' > max l of the tile, or
   // if every |m| of the m-tile exceeds it (Z_{m l m'} is read only for l >= |m|)
@@ -120,19 +121,19 @@ struct SynthesisProb {
     kb = rg.x * TC_CHUNK_K;
     ke = amin > lhi ? kb : (rg.x + rg.y) * TC_CHUNK_K;
   }
+  // Pair loads: lane r & 3 = j of the four rows r = 4p .. 4p+3 (m = mi0 + 2p and its pair
+  // partner, Re and Im) takes the 16 bytes of both columns at ni = k0 + 4q + j, i.e. the four
+  // rows at one K; the engine transposes the group (rows out of range are zeroed by a_rows).
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
-    const int mi = mi0 + (r >> 1);
-    const cx<float>* plane = Y + (size_t)mp * cs.pitch();
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int ni = k0 + 4 * q + i;
-      float v = 0.f;
-      if (mi < cs.Mc && ni < cs.Nc) {
-        const cx<float> y = plane[cs.col(mi, ni)];
-        v = (r & 1) ? y.im : y.re;
-      }
-      x[i] = v;
-    }
+    const int mi = mi0 + ((r >> 2) << 1);  // first m of the pair (mi0 is even)
+    const int ni = k0 + 4 * q + (r & 3);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mi < cs.Mc && ni < cs.Nc)  // the partner column of an odd Mc is in the plane's pitch
+      v = *reinterpret_cast<const float4*>(Y + (size_t)mp * cs.pitch() + cs.col(mi, ni));
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  }
+  __device__ void a_rows(int mi0, int r, float* x) const {
+    if (mi0 + (r >> 1) >= cs.Mc) x[0] = x[1] = x[2] = x[3] = 0.f;
   }
   __device__ void b_tiles(int mp, int l0, int k0, const void*& hi, const void*& lo) const {
     tab_tiles(tb, mp, l0 / BNC, k0, hi, lo);

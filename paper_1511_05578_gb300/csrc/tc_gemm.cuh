@@ -161,6 +161,35 @@ __device__ __forceinline__ float dq(const float* __restrict__ Q, int Lmax, int a
 // with cp.async.bulk on the stage's full barrier:
 //   Prob::b_tiles(z, c0, k0, hi, lo)          device addresses of the hi and lo tiles (B_BYTES each)
 // ---------------------------------------------------------------------------
+// Prob::kPairLoads: a4 gives, to lane j of each group of four lanes (four
+// consecutive rows r = 4p + j), the four rows 4p .. 4p+3 at the one K index 4q + j; the
+// producers transpose the group's 4 x 4 values by shuffles (Prob::a_rows then zeroes rows out
+// of range) before storing, so that one 16-byte load per lane feeds four rows.
+template <class P, class = void> struct PairLoads { static constexpr bool value = false; };
+template <class P> struct PairLoads<P, std::enable_if_t<P::kPairLoads>> { static constexpr bool value = true; };
+// 4 x 4 transpose within each group of four lanes: lane j holds x[i] = M[i][j] on entry and
+// x[i] = M[j][i] on exit. Lane j needs M[j][s] = x_s[j] from lane s. With a[k] = x[(j - k) & 3]
+// every round k sends a fixed index: lane j reads a[k] of lane (j + k) & 3, which is
+// M[j][(j + k) & 3], and rotating those back by j gives the row.
+__device__ __forceinline__ void rot4(float (&x)[4], int by) {  // x[k] <- x[(k - by) & 3]
+  float t[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) t[k] = (by & 1) ? x[(k + 3) & 3] : x[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) x[k] = (by & 2) ? t[(k + 2) & 3] : t[k];
+}
+__device__ __forceinline__ void transpose4(float (&x)[4], int lane) {
+  const int j = lane & 3, g = lane & ~3;
+  float a[4] = {x[0], x[3], x[2], x[1]};  // a[k] = x[(-k) & 3]
+  rot4(a, j);                             // a[k] = x[(j - k) & 3]
+  float b[4];
+  b[0] = a[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) b[k] = __shfl_sync(0xffffffffu, a[k], g | ((j + k) & 3));
+  rot4(b, j);  // b[i] = M[j][i]
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = b[i];
+}
 template <class P, class = void> struct BulkB { static constexpr bool value = false; };
 template <class P> struct BulkB<P, std::enable_if_t<P::kBulkB>> { static constexpr bool value = true; };
 // Prob::kBulkA (persistent engine only): the A tiles are also in tables, Prob::a_tiles(z, r0, k0, hi, lo)
@@ -249,6 +278,10 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
       const int it = tid + i * NT;
+      if constexpr (PairLoads<Prob>::value) {
+        transpose4(xa[i], tid & 31);
+        pb.a_rows(r0, it % BM, xa[i]);
+      }
       put4(st, st + A_BYTES, it % BM, it / BM, xa[i]);
     }
     if constexpr (!BULK) {
@@ -482,7 +515,13 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
         }
         unsigned char* st = base + s * STAGE_BYTES;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) put4(st, st + A_BYTES, pr, pq + q * PQ, xs[0][q]);
+        for (int q = 0; q < NQ; ++q) {
+          if constexpr (PairLoads<Prob>::value) {
+            transpose4(xs[0][q], lane);
+            pb.a_rows(r0, pr, xs[0][q]);
+          }
+          put4(st, st + A_BYTES, pr, pq + q * PQ, xs[0][q]);
+        }
         fence_proxy_async();
         __syncwarp();
         if (lane == 0) mbar_arrive(&a_full[s]);
