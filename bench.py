@@ -60,6 +60,9 @@ def parse():
                     help="maps per analysis/synthesis call (a divisor of B); with 2 or more the plan runs two "
                          "maps at once on two instances where memory allows")
     ap.add_argument("--tune", action="store_true", help="create the plan with CRV_F_TUNE (autotuned workers and ring chunks)")
+    ap.add_argument("--graph", action="store_true",
+                    help="capture one step (all its calls) into a CUDA graph after the warm-up and replay it "
+                         "(no host launch cost per kernel; small band limits)")
     ap.add_argument("--serving-requests", type=int, default=24,
                     help="requests of the serving leg (Poisson arrivals; 0 = skip)")
     ap.add_argument("--serving-rate", type=float, default=0.5, help="mean arrivals per second of the serving leg")
@@ -383,6 +386,7 @@ def config_dict(args):
                         + (", unrotated curvelets (O(L^3) single-term contraction)" if args.unrotated else ""),
             "L": args.L, "maps_per_gpu": args.B, "lambda": args.lam, "J0": args.J0, "spin": 0, "real": True,
             "precision": args.mode, "unrotated": bool(args.unrotated), "maps_per_call": args.maps_per_call if not args.batch_calls else args.B,
+            "cuda_graph": bool(args.graph),
             "l2": "inputs larger than L2 (537 MB maps per step; W_j 36.8 GB per map)" if args.L >= 1024 else
                   "inputs of a step smaller than L2 at this band limit"}
 
@@ -450,6 +454,19 @@ def main():
     # accuracy of the round trip on this rank's last map (FP32 W / mixed: <= 1e-5 relative)
     recon = float(torch.linalg.vector_norm(out[-1] - maps[-1]) / torch.linalg.vector_norm(maps[-1]))
 
+    graph = None
+    if args.graph:
+        # one step's calls captured once (the plan's per-call path allocates nothing and never
+        # synchronises, its worker streams fork and join by events), replayed every step
+        graph = torch.cuda.CUDAGraph()
+        lc0 = crv.crv_launch_count()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(graph, stream=stream):
+                step(maps, out)
+        graph_launches = crv.crv_launch_count() - lc0  # kernels in the graph (counted at capture)
+        with torch.cuda.stream(stream):
+            graph.replay()  # one more warm-up, as the replays below
+        torch.cuda.synchronize()
     kinds = crv.crv_profile_kinds()
     l0 = crv.crv_launch_count()
     clocks = ClockSampler(local)
@@ -462,13 +479,18 @@ def main():
     for _ in range(args.steps):
         a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for b in range(0, B, nb):  # one step = all B maps; per-call events give the latency distribution
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            crv.crv_analysis(plan.handle, maps[b:b + nb], W, Wphi, nb, stream.cuda_stream)
-            crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + nb], nb, stream.cuda_stream)
-            e1.record(stream)
-            per_map.append((e0, e1))
+        if graph is not None:
+            with torch.cuda.stream(stream):
+                graph.replay()
+            per_map.append((a, None))
+        else:
+            for b in range(0, B, nb):  # one step = all B maps; per-call events give the latency distribution
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                crv.crv_analysis(plan.handle, maps[b:b + nb], W, Wphi, nb, stream.cuda_stream)
+                crv.crv_synthesis(plan.handle, W, Wphi, out[b:b + nb], nb, stream.cuda_stream)
+                e1.record(stream)
+                per_map.append((e0, e1))
         b_.record(stream)
         per_step.append((a, b_))
     ev1.record(stream)
@@ -476,6 +498,8 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = crv.crv_launch_count() - l0
+    if graph is not None:
+        launches = graph_launches * args.steps  # replays launch the captured kernels
     ms_total = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b_) for a, b_ in per_step]
     # per-kind device times from a pass of their own after the timed region (no event records
@@ -500,6 +524,8 @@ def main():
     value = whole_job_rate(world, B, args.steps, t_max)
 
     # per-map latency (p50 / p99) from the per-map events of the timed steps
+    if graph is not None:  # a graph replay is one step: its duration is the latency
+        per_map = per_step
     lat_ms = sorted(a.elapsed_time(b_) for a, b_ in per_map)
     p50 = lat_ms[len(lat_ms) // 2]
     p99 = lat_ms[min(len(lat_ms) - 1, int(math.ceil(0.99 * len(lat_ms))) - 1)]
@@ -694,7 +720,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f64", "data": "synthetic",
         "config": config_dict(args), "p50_ms": p50, "p99_ms": p99,
-        "latency_unit": "ms per map (analysis+synthesis)" if nb == 1 else f"ms per call of {nb} maps (analysis+synthesis)",
+        "latency_unit": (f"ms per step ({B} maps, one CUDA graph replay)" if args.graph else
+                         "ms per map (analysis+synthesis)" if nb == 1 else f"ms per call of {nb} maps (analysis+synthesis)"),
         "launches_per_map": launches / (args.steps * B), "plan_tuning": tuning,
         "roundtrip_rel_l2": recon, "gpu_launches": launches, "clocks": clk, "roofline": roof, "roofline_map": roof_map,
         "e2e": e2e,
