@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/crv.h"
 #include "contract.cuh"
 #include "rotate.cuh"
@@ -23,6 +25,21 @@
 namespace crv {
 
 static thread_local std::string g_err;
+
+// NVTX range over a scope: the ABI calls, plan creation and the per-scale phases show as named
+// ranges in Nsight tools (ncu --nvtx filters on them); without a tool attached a push/pop
+// is a no-op.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* what, int j) {
+    char b[64];
+    snprintf(b, sizeof b, "%s j=%d", what, j);
+    nvtxRangePushA(b);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -734,6 +751,7 @@ static bool ring_inverse(crv_plan_s* p, const FftSet& fs, const ColSet& cs, cons
 
 template <class T, class OutT>
 static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, OutT* W, cudaStream_t st) {
+  NvtxRange nv("analysis scale", j);
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
   const FftSet& fs = p->fft.at(Lb);
   ColSet cs = p->colset(Lb);
@@ -792,6 +810,7 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
 
 template <class T, class InT>
 static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double>* flm, cudaStream_t st) {
+  NvtxRange nv("synthesis scale", j);
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
   const FftSet& fs = p->fft.at(Lb);
   ColSet cs = p->colset(Lb);
@@ -1344,6 +1363,7 @@ static int tune_plan(crv_plan_s* p, cudaStream_t st) {
 
 int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int nrule, unsigned flags,
                     int max_batch, void* stream) {
+  NvtxRange nv("crv_plan_create");
   if (!out) return fail(CRV_EINVAL, "out is NULL");
   *out = nullptr;
   if (L < 2 || L > 4096) return fail(CRV_EINVAL, "L must be in [2, 4096]");
@@ -1744,6 +1764,7 @@ static int check_rotate(crv_plan_t p, int j, int B, const void* a, const void* b
 }
 
 int crv_rotate_wigner(crv_plan_t p, int j, const void* wt, void* w, int B, void* stream) {
+  NvtxRange nv("crv_rotate_wigner");
   int s = check_rotate(p, j, B, wt, w);
   if (s) return s;
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
@@ -1755,6 +1776,7 @@ int crv_rotate_wigner(crv_plan_t p, int j, const void* wt, void* w, int B, void*
 }
 
 int crv_rotate_wigner_adjoint(crv_plan_t p, int j, const void* w, void* wt, int B, void* stream) {
+  NvtxRange nv("crv_rotate_wigner_adjoint");
   int s = check_rotate(p, j, B, w, wt);
   if (s) return s;
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
@@ -1766,6 +1788,7 @@ int crv_rotate_wigner_adjoint(crv_plan_t p, int j, const void* w, void* wt, int 
 }
 
 int crv_sht_fwd(crv_plan_t p, const void* map, void* flm, int B, void* stream) {
+  NvtxRange nv("crv_sht_fwd");
   int s = check_batch(p, B, map, flm);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
@@ -1776,6 +1799,7 @@ int crv_sht_fwd(crv_plan_t p, const void* map, void* flm, int B, void* stream) {
 }
 
 int crv_sht_inv(crv_plan_t p, const void* flm, void* map, int B, void* stream) {
+  NvtxRange nv("crv_sht_inv");
   int s = check_batch(p, B, flm, map);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
@@ -1786,6 +1810,7 @@ int crv_sht_inv(crv_plan_t p, const void* flm, void* map, int B, void* stream) {
 }
 
 int crv_analysis_lm(crv_plan_t p, const void* flm, void* const* W, void* Wphi, int B, void* stream) {
+  NvtxRange nv("crv_analysis_lm");
   int s = check_batch(p, B, flm, W);
   if (s) return s;
   return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
@@ -1794,6 +1819,7 @@ int crv_analysis_lm(crv_plan_t p, const void* flm, void* const* W, void* Wphi, i
 }
 
 int crv_analysis(crv_plan_t p, const void* map, void* const* W, void* Wphi, int B, void* stream) {
+  NvtxRange nv("crv_analysis");
   int s = check_batch(p, B, map, W);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
@@ -1804,6 +1830,7 @@ int crv_analysis(crv_plan_t p, const void* map, void* const* W, void* Wphi, int 
 }
 
 int crv_synthesis_lm(crv_plan_t p, const void* const* W, const void* Wphi, void* flm, int B, void* stream) {
+  NvtxRange nv("crv_synthesis_lm");
   int s = check_batch(p, B, W, flm);
   if (s) return s;
   return run_maps(p, B, (cudaStream_t)stream, [&](crv_plan_s* q, int b, cudaStream_t st) {
@@ -1812,6 +1839,7 @@ int crv_synthesis_lm(crv_plan_t p, const void* const* W, const void* Wphi, void*
 }
 
 int crv_synthesis(crv_plan_t p, const void* const* W, const void* Wphi, void* map, int B, void* stream) {
+  NvtxRange nv("crv_synthesis");
   int s = check_batch(p, B, W, map);
   if (s) return s;
   const size_t me = (size_t)p->L * (2 * p->L - 1) * (p->real ? 1 : 2);
