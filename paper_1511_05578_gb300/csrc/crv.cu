@@ -585,12 +585,12 @@ static bool run_dft_nt(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld,
   return launch_ok(kind_name(kind));
 }
 // FP32: 256 threads (two blocks per SM); FP64: 256 threads, one block per SM. The lengths
-// of the two largest band limits get kernels compiled for their P.
+// of the two largest band limits get kernels compiled for their P (both precisions).
 template <class T, bool COLS, class Ld, class St>
 static bool run_dft(int kind, const DftTab<T>& tb, int sign, int nseq, Ld ld, St st, cudaStream_t s) {
   if (nseq <= 0) return true;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_dft_nt<T, 256, COLS, 4096>(kind, tb, sign, nseq, ld, st, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_dft_nt<T, 256, COLS, 2048>(kind, tb, sign, nseq, ld, st, s);
+  if (tb.P == 4096) return run_dft_nt<T, 256, COLS, 4096>(kind, tb, sign, nseq, ld, st, s);
+  if (tb.P == 2048) return run_dft_nt<T, 256, COLS, 2048>(kind, tb, sign, nseq, ld, st, s);
   return run_dft_nt<T, 256, COLS, 0>(kind, tb, sign, nseq, ld, st, s);
 }
 template <class T, class Ld, class St>
@@ -626,8 +626,8 @@ static bool run_beta_synth(const DftTab<T>& tb, int Lb, int ncols, const cx<T>* 
                            cudaStream_t s, PairMap pm = PairMap()) {
   if (ncols <= 0) return true;
   constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_synth_nt<T, NT, 4096>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_synth_nt<T, NT, 2048>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
+  if (tb.P == 4096) return run_beta_synth_nt<T, NT, 4096>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
+  if (tb.P == 2048) return run_beta_synth_nt<T, NT, 2048>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
   return run_beta_synth_nt<T, NT, 0>(tb, Lb, ncols, X, Y, cs, kind, pm, s);
 }
 
@@ -655,8 +655,8 @@ static bool run_beta_quad(const FftSet& fs, int Lb, int ncols, const cx<T>* Xb, 
   if (ct.Q != tb.P) { g_err = "beta quadrature needs Q == P"; return false; }
   if (ncols <= 0) return true;
   constexpr int NT = sizeof(T) == 4 ? 512 : 256;
-  if (sizeof(T) == 4 && tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
-  if (sizeof(T) == 4 && tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
+  if (tb.P == 4096) return run_beta_quad_nt<T, NT, 4096>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
+  if (tb.P == 2048) return run_beta_quad_nt<T, NT, 2048>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
   return run_beta_quad_nt<T, NT, 0>(tb, ct, Lb, ncols, Xb, Y, cs, scale, pa, pb, pc, pm, kind, s);
 }
 
