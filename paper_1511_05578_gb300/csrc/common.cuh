@@ -60,6 +60,49 @@ template <class T> __host__ __device__ __forceinline__ cx<T> mul_ipow(cx<T> a, i
 }
 __host__ __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 
+// Double-float: an unevaluated sum hi + lo of two FP32 values (|lo| <= ulp(hi)/2), about 48
+// significant bits, with additions and multiplications in FP32 instructions (Knuth's two-sum
+// and the FMA product error, then renormalised). The FP64 plans run their largest Wigner FFTs
+// in it: GB300 issues FP32 at many times its FP64 rate. The error-free steps must not be fused
+// into FMAs or reassociated: on the device they use the _rn intrinsics, which the compiler never
+// contracts. (Host code only converts to and from double.)
+struct df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ df(int x) : hi((float)x), lo(0.f) {}
+  __host__ __device__ df(float x) : hi(x), lo(0.f) {}
+  __host__ __device__ df(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ df operator+(df a, df b) {
+  const float s = __fadd_rn(a.hi, b.hi), bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));  // s + e = a.hi + b.hi
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  df r;
+  r.hi = __fadd_rn(s, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+  return r;
+}
+__device__ __forceinline__ df operator-(df a) {
+  df r;
+  r.hi = -a.hi;
+  r.lo = -a.lo;
+  return r;
+}
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // p + e = a.hi b.hi exactly
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  df r;
+  r.hi = __fadd_rn(p, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, p));
+  return r;
+}
+#endif
+
 // Exact division of 32-bit unsigned n by a runtime constant d (1 <= d < 2^32) with a
 // 64-bit reciprocal M = floor((2^64-1)/d) + 1: n / d = mulhi64(M, n) (Lemire et al.,
 // "Faster remainder by direct computation", 2019).
@@ -96,6 +139,9 @@ void count_launch();
 // SM count, and a kernel's dynamic shared-memory limit raised once on each device.
 int device_sms();
 bool func_attr_once(const void* kernel, int smem_bytes);
+// Preferred shared-memory carveout of a kernel for `blocks` blocks of `bytes` each (once per
+// device): the rest of the unified L1 stays cache.
+void carveout_for(const void* kernel, size_t bytes, int blocks);
 // Check the last launch; on failure store a message and return false.
 bool launch_ok(const char* what);
 

@@ -1,6 +1,6 @@
 // libcrv host side: plan construction, per-scale pipelines and the C ABI of
 // include/crv.h. Device work lives in delta.cu, transforms.cuh, contract.cuh,
-// tc_contract.cu, tc_ozaki.cu and rotate.cu.
+// tc_contract.cu, tc_ozaki.cu, df_fft.cu and rotate.cu.
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -12,6 +12,7 @@
 #include <atomic>
 #include <set>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -21,6 +22,7 @@
 #include "rotate.cuh"
 #include "tc_contract.cuh"
 #include "tc_ozaki.cuh"
+#include "df_fft.cuh"
 
 namespace crv {
 
@@ -231,8 +233,8 @@ using namespace crv;
 // The plan
 // ---------------------------------------------------------------------------
 struct FftSet {
-  DftTab<double> d; DftTab<float> f;
-  CorrTab<double> cd; CorrTab<float> cf;
+  DftTab<double> d; DftTab<float> f; DftTab<df> x;  // x: double-float (FP64 plans, P = 4096)
+  CorrTab<double> cd; CorrTab<float> cf; CorrTab<df> cx2;
 };
 
 // Device allocations of the read-only tables of a plan (Delta, Delta Psi tensor-core
@@ -301,6 +303,7 @@ struct crv_plan_s {
   // contractions, and the layout of the per-map A tables with the passes over m' that keep
   // one pass's A table within oz_cap chunks (one buffer per instance)
   bool use_oz = false;
+  bool df_fft = false;  // FP64 plans: the P = 4096 Wigner FFTs of real signals in double-float
   struct OzA {
     const long long* base = nullptr;
     const int2* range = nullptr;
@@ -415,9 +418,11 @@ static OzTab oz_pass(const crv_plan_s* p, const crv_plan_s::OzA& a, int i) {
 
 template <class T> static const DftTab<T>& dft_of(const FftSet& s);
 template <> const DftTab<double>& dft_of<double>(const FftSet& s) { return s.d; }
+template <> const DftTab<df>& dft_of<df>(const FftSet& s) { return s.x; }
 template <> const DftTab<float>& dft_of<float>(const FftSet& s) { return s.f; }
 template <class T> static const CorrTab<T>& corr_of(const FftSet& s);
 template <> const CorrTab<double>& corr_of<double>(const FftSet& s) { return s.cd; }
+template <> const CorrTab<df>& corr_of<df>(const FftSet& s) { return s.cx2; }
 template <> const CorrTab<float>& corr_of<float>(const FftSet& s) { return s.cf; }
 
 static int build_fft(crv_plan_s* p, int Lb) {
@@ -496,6 +501,20 @@ static int build_fft(crv_plan_s* p, int Lb) {
   up(bquad, d, f); s.d.bquad = d; s.f.bquad = f;
   s.cd.Q = s.cf.Q = Q;
   up(wv, d, f); s.cd.what = d; s.cf.what = f;
+  if (P == 4096 && !p->mixed) {  // double-float copies (hi + lo of every double) for the FP64 plans
+    auto upx = [&](const std::vector<std::complex<double>>& v) -> const cx<df>* {
+      cx<df>* dx = p->talloc<cx<df>>(v.size(), &st);
+      if (st != CRV_OK) return nullptr;
+      std::vector<cx<df>> hx(v.size());
+      for (size_t i = 0; i < v.size(); ++i) hx[i] = mk(df(v[i].real()), df(v[i].imag()));
+      cudaMemcpy(dx, hx.data(), v.size() * sizeof(cx<df>), cudaMemcpyHostToDevice);
+      return dx;
+    };
+    s.x.N = N; s.x.P = P; s.x.R0 = R0; s.x.nst = nst;
+    s.x.stw = upx(stw); s.x.chirp = upx(chirp); s.x.khat_f = upx(kf); s.x.khat_i = upx(ki);
+    s.x.hphase = upx(hp); s.x.bsyn = upx(bsyn); s.x.bquad = upx(bquad);
+    s.cx2.Q = Q; s.cx2.what = upx(wv);
+  }
   if (st != CRV_OK) return st;
   p->fft[Lb] = s;
   return CRV_OK;
@@ -546,7 +565,7 @@ static bool set_smem(K kernel, size_t bytes) {
 // Shared-memory carveout of a kernel set to what `blocks` resident blocks of `bytes` each need
 // (and no more), so that the rest of the SM's unified L1/shared storage stays L1: the ring
 // transforms' strided loads depend on L1 capacity. Once per kernel and device.
-static void carveout_for(const void* kernel, size_t bytes, int blocks) {
+void crv::carveout_for(const void* kernel, size_t bytes, int blocks) {
   int dev = 0;
   cudaGetDevice(&dev);
   static std::set<std::pair<const void*, int>> done;
@@ -749,6 +768,92 @@ static bool ring_inverse(crv_plan_s* p, const FftSet& fs, const ColSet& cs, cons
   return run_cols<T>(K_RING_INV_M, dft_of<T>(fs), +1, nr * N, lm, sw, st);
 }
 
+// Values of an FP64 plan's (m, n, m') volume between FP64 (contractions) and double-float
+// (FFTs), in place: both take 16 bytes per complex value.
+template <bool TO_DF>
+__global__ void convert_volume_kernel(void* v, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (TO_DF) {
+      const cx<double> a = reinterpret_cast<cx<double>*>(v)[i];
+      reinterpret_cast<cx<df>*>(v)[i] = mk(df(a.re), df(a.im));
+    } else {
+      const cx<df> a = reinterpret_cast<cx<df>*>(v)[i];
+      reinterpret_cast<cx<double>*>(v)[i] = mk((double)a.re, (double)a.im);
+    }
+  }
+}
+template <bool TO_DF>
+static bool convert_volume(void* v, size_t n, cudaStream_t st) {
+  if (n == 0) return true;
+  const int grid = (int)std::min<size_t>((n + 255) / 256, (size_t)num_sms() * 8);
+  KTimer kt(K_MISC, st);
+  convert_volume_kernel<TO_DF><<<grid, 256, 0, st>>>(v, n);
+  kt.done();
+  return launch_ok("convert_volume_kernel");
+}
+
+// Whether scale j of a plan runs its FFTs in double-float: FP64 plans, real signals, rotated
+// coefficients, the P = 4096 length (band limit 1024), with the FP64 tables split at creation.
+static bool df_scale(const crv_plan_s* p, int j) {
+  return p->df_fft && p->real && !p->unrot && p->fft.at(p->Lj[j]).x.P == 4096;
+}
+
+// The FFT steps of the analysis of scale j in double-float (real signals, P = 4096): the steps
+// of the FP64 path (beta synthesis, the m step on the n >= 0 columns, the n step with real output
+// in row pairs) on the kernels compiled in df_fft.cu.
+static bool analysis_ffts_df(crv_plan_s* p, int j, double* W, cudaStream_t st) {
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  const DftTab<df>& tb = p->fft.at(Lb).x;
+  const ColSet cs = p->colset(Lb);
+  cx<df>* X = (cx<df>*)p->wX;
+  cx<df>* Xb = (cx<df>*)p->wXb;
+  cx<df>* R = (cx<df>*)p->wR;
+  if (!df_beta_synth(tb, Lb, (int)cs.pitch(), X, Xb, cs, st)) return false;
+  const int Rr = ring_chunk(p, Lb, sizeof(cx<df>));
+  const size_t wstride = (size_t)N * N;
+  const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0, npair = (N + 1) / 2;
+  for (int b0 = 0; b0 < Lb; b0 += Rr) {
+    const int nr = std::min(Rr, Lb - b0);
+    if (Nh > 0) {
+      LdRingMHalf<df, false> lm{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, FastDiv((uint32_t)Nh), 0};
+      StRingMHalf<df> sm{R, N, Nh, FastDiv((uint32_t)Nh), Nh, 0};
+      if (!df_ring_m(tb, nr * Nh, lm, sm, st)) return false;
+    }
+    LdRingNHerm<df, false> ln{R, N, Nh, cs.nstep, npair, FastDiv((uint32_t)npair), 0};
+    StWRowPair<df, double> sw{W + (size_t)b0 * wstride, N, npair, FastDiv((uint32_t)npair)};
+    if (!df_ring_n(tb, nr * npair, ln, sw, st)) return false;
+  }
+  return true;
+}
+
+// The FFT steps of the synthesis of scale j in double-float (real signals, P = 4096): g step on
+// real row pairs, a step on the n >= 0 columns, beta quadrature into the Y planes.
+static bool synthesis_ffts_df(crv_plan_s* p, int j, const double* W, cudaStream_t st) {
+  const int Lb = p->Lj[j], N = 2 * Lb - 1;
+  const FftSet& fs = p->fft.at(Lb);
+  const DftTab<df>& tb = fs.x;
+  const ColSet cs = p->colset(Lb);
+  cx<df>* Y = (cx<df>*)p->wX;
+  cx<df>* Xb = (cx<df>*)p->wXb;
+  cx<df>* R = (cx<df>*)p->wR;
+  const int Rr = ring_chunk(p, Lb, sizeof(cx<df>));
+  const size_t wstride = (size_t)N * N;
+  const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;
+  const df inv = df(1.0 / N);
+  for (int b0 = 0; b0 < Lb; b0 += Rr) {
+    const int nr = std::min(Rr, Lb - b0), nrows = nr * N;
+    LdWRowPair<df, double> lw{W + (size_t)b0 * wstride, N, nrows};
+    StRingNPairHalf<df> sn{R, Nh, cs.nstep, N, nrows, inv, 0};
+    if (!df_ring_g(tb, (nrows + 1) / 2, lw, sn, st)) return false;
+    if (Nh > 0) {
+      LdRingAHalf<df> la{R, N, Nh, FastDiv((uint32_t)Nh), Nh, 0};
+      StRingAHalf<df> sa{Xb + (size_t)b0 * cs.pitch(), cs, ni0, N, Nh, inv, FastDiv((uint32_t)Nh), 0};
+      if (!df_ring_a(tb, nr * Nh, la, sa, st)) return false;
+    }
+  }
+  return df_beta_quad(tb, fs.cx2, Lb, (int)cs.pitch(), Xb, Y, cs, df(4 * M_PI * M_PI), 1, -1, 0, st);
+}
+
 template <class T, class OutT>
 static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, OutT* W, cudaStream_t st) {
   NvtxRange nv("analysis scale", j);
@@ -791,6 +896,12 @@ static bool wigner_analysis_scale(crv_plan_s* p, int j, const cx<double>* flm, O
     kt.done();
     if (!launch_ok("contract_analysis_kernel")) return false;
   }
+  if constexpr (sizeof(T) == 8 && std::is_same<OutT, double>::value) {
+    if (df_scale(p, j)) {  // X into double-float in place, then the FFTs on the FP32 pipe
+      if (!convert_volume<true>(p->wX, (size_t)Lb * cs.pitch(), st)) return false;
+      return analysis_ffts_df(p, j, W, st);
+    }
+  }
   const int ncols = (int)cs.pitch();
   const PairMap pm = p->unrot ? PairMap{p->dpmap[j], p->npmap[j]} : PairMap();
   if (!run_beta_synth<T>(dft_of<T>(fs), Lb, ncols, X, Xb, cs, K_BETA_SYNTH, st, pm)) return false;
@@ -822,7 +933,15 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   const int ni0 = -cs.n0 / cs.nstep, Nh = cs.Nc - ni0;  // columns n >= 0
   // unrotated plans: only the columns |n| >= nlo are needed downstream
   const int nlo = p->unrot ? p->nlo[j] : 0, h0 = std::min(nlo, Nh), Nhs = Nh - h0;
-  for (int b0 = 0; b0 < Lb; b0 += Rr) {
+  bool df_done = false;
+  if constexpr (sizeof(T) == 8 && std::is_same<InT, double>::value) {
+    if (df_scale(p, j)) {  // the FFTs on the FP32 pipe, then Y back to FP64 in place
+      if (!synthesis_ffts_df(p, j, W, st)) return false;
+      if (!convert_volume<false>(p->wX, (size_t)Lb * cs.pitch(), st)) return false;
+      df_done = true;
+    }
+  }
+  for (int b0 = 0; b0 < Lb && !df_done; b0 += Rr) {
     const int nr = std::min(Rr, Lb - b0);
     if (p->real) {
       // g step on real rows in pairs keeping n >= 0, then the a step on those columns,
@@ -847,7 +966,7 @@ static bool wigner_synthesis_scale(crv_plan_s* p, int j, const InT* W, cx<double
   }
   const int ncols = (int)cs.pitch();
   const PairMap pm = p->unrot ? PairMap{p->dpmap[j], p->npmap[j]} : PairMap();
-  if (!run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st, pm)) return false;
+  if (!df_done && !run_beta_quad<T>(fs, Lb, ncols, Xb, Y, cs, (T)(4 * M_PI * M_PI), 1, -1, 0, st, pm)) return false;
   if (p->unrot) {
     // Xb is consumed by the beta quadrature: its buffer holds the per-chunk sums
     const int nchunk = (Lb + US_MPC - 1) / US_MPC;
@@ -1395,6 +1514,10 @@ int crv_plan_create(crv_plan_t* out, int L, double lambda, int J0, int spin, int
   p->real = flags & CRV_F_REAL; p->mixed = flags & CRV_F_MIXED; p->wfp32 = flags & CRV_F_W_FP32;
   p->unrot = flags & CRV_F_UNROTATED;
   p->use_oz = flags & CRV_F_FP64_TC;
+  {
+    const char* e = getenv("CRV_FP64_FFT");  // "double" keeps every FFT of the FP64 plans in FP64
+    p->df_fft = !p->mixed && !(e && std::strcmp(e, "double") == 0);
+  }
   p->guard = flags & CRV_F_GUARD;
   p->Lphi = std::max(1, ceil_pow(lambda, J0));
   p->Lphi = std::min(p->Lphi, L);
