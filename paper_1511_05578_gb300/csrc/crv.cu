@@ -501,7 +501,7 @@ static int build_fft(crv_plan_s* p, int Lb) {
   up(bquad, d, f); s.d.bquad = d; s.f.bquad = f;
   s.cd.Q = s.cf.Q = Q;
   up(wv, d, f); s.cd.what = d; s.cf.what = f;
-  if (P == 4096 && !p->mixed) {  // double-float copies (hi + lo of every double) for the FP64 plans
+  if ((P == 4096 || P == 2048) && !p->mixed) {  // double-float copies (hi + lo of every double), FP64 plans
     auto upx = [&](const std::vector<std::complex<double>>& v) -> const cx<df>* {
       cx<df>* dx = p->talloc<cx<df>>(v.size(), &st);
       if (st != CRV_OK) return nullptr;
@@ -793,14 +793,16 @@ static bool convert_volume(void* v, size_t n, cudaStream_t st) {
 }
 
 // Whether scale j of a plan runs its FFTs in double-float: FP64 plans, real signals, rotated
-// coefficients, the P = 4096 length (band limit 1024), with the FP64 tables split at creation.
+// coefficients, the lengths P = 4096 and 2048 (band limits 513..1024 and 257..512), with the FP64
+// tables split at creation.
 static bool df_scale(const crv_plan_s* p, int j) {
-  return p->df_fft && p->real && !p->unrot && p->fft.at(p->Lj[j]).x.P == 4096;
+  const int P = p->fft.at(p->Lj[j]).x.P;
+  return p->df_fft && p->real && !p->unrot && (P == 4096 || P == 2048);
 }
 
-// The FFT steps of the analysis of scale j in double-float (real signals, P = 4096): the steps
+// The FFT steps of the analysis of scale j in double-float (real signals, P = 4096 or 2048): the steps
 // of the FP64 path (beta synthesis, the m step on the n >= 0 columns, the n step with real output
-// in row pairs) on the kernels compiled in df_fft.cu.
+// in row pairs) on the kernels compiled in df_fft.cu and df_fft2048.cu.
 static bool analysis_ffts_df(crv_plan_s* p, int j, double* W, cudaStream_t st) {
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
   const DftTab<df>& tb = p->fft.at(Lb).x;
@@ -826,7 +828,7 @@ static bool analysis_ffts_df(crv_plan_s* p, int j, double* W, cudaStream_t st) {
   return true;
 }
 
-// The FFT steps of the synthesis of scale j in double-float (real signals, P = 4096): g step on
+// The FFT steps of the synthesis of scale j in double-float (real signals, P = 4096 or 2048): g step on
 // real row pairs, a step on the n >= 0 columns, beta quadrature into the Y planes.
 static bool synthesis_ffts_df(crv_plan_s* p, int j, const double* W, cudaStream_t st) {
   const int Lb = p->Lj[j], N = 2 * Lb - 1;
