@@ -1151,6 +1151,7 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
       cudaMemcpy(drange, range.data(), range.size() * sizeof(int2), cudaMemcpyHostToDevice);
       TcTab t;
       t.hi = hi; t.lo = lo; t.base = dbase; t.range = drange; t.ntiles = ntiles;
+      for (const int2& r : range) t.kmax = std::max(t.kmax, r.y);
       const bool ok = dir == 0 ? tc_fill_analysis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st)
                                : tc_fill_synthesis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st);
       if (!ok) return CRV_ECUDA;

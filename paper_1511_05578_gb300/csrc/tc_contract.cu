@@ -37,6 +37,7 @@ __device__ __forceinline__ void tab_tiles(const TcTab& tb, int mp, int tile, int
 struct AnalysisProb {
   static constexpr bool kBulkB = true;
   const float* Q; int Lmax; const cx<float>* flm; TcTab tb; int Lb; ColSet cs; cx<float>* X;
+  bool split = false;  // hi*hi apart from the corrections (scales with long l runs)
   // K chunks: the table's run for (m', n-tile), skipping chunks below min |m| of the m-tile
   __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
     mp = bz; mi0 = by * (BM / 2); n0i = bx * BNC;
@@ -378,6 +379,7 @@ static int sm_count() { return device_sms(); }
 bool tc_analysis(const float* Q32, int Lmax, const cx<float>* flm, TcTab tb, int Lb, ColSet cs, cx<float>* X,
                  int* err, int* ctr, cudaStream_t st, TcATab ta) {
   tc::AnalysisProb pb{Q32, Lmax, flm, tb, Lb, cs, X};
+  pb.split = tb.kmax * TC_CHUNK_K > TC_SPLIT_K;
   dim3 grid(tb.ntiles, (cs.Mc + tc::BM / 2 - 1) / (tc::BM / 2), Lb);
   if (ta.hi && use_ws()) {
     // A operand into its tables first (one pass over Delta and f), then both operands by copy

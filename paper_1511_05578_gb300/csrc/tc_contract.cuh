@@ -23,8 +23,15 @@ struct TcTab {
   const long long* base = nullptr;
   const int2* range = nullptr;
   int ntiles = 0;
+  int kmax = 0;  // the longest run of K chunks over (m', tile)
 };
 constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 16, TC_CHUNK_FLOATS = TC_TILE_ROWS * TC_CHUNK_K;
+// The tensor core's FP32 accumulation behaves like truncation, so the error of a long K sum
+// grows with the number of MMA steps into it (three per K-step of 8 with one accumulator).
+// Analysis scales whose K runs exceed TC_SPLIT_K take the hi*hi products and the corrections
+// in separate accumulators (one step per K-step at full size), at the cost of a single-
+// buffered accumulator pair; the shorter runs stay double-buffered.
+constexpr int TC_SPLIT_K = 512;
 
 // Per-map A operand of the analysis contraction for one scale (rebuilt for every map and
 // scale): for every (m', m-tile of 64 values of m) the run of 16-wide K chunks from

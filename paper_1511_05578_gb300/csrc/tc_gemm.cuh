@@ -3,7 +3,8 @@
 // D[128 x BN] = sum_k A[128 x k] B[BN x k]^T with FP32 operands produced on the fly by a
 // problem object or copied from pre-split tables. Each operand x is split into TF32
 // hi = rna(x), lo = rna(x - hi); a K-step issues hi*hi + hi*lo + lo*hi into one FP32 TMEM
-// accumulator (split-FP32, ~2^-22 per product). Operand stages sit in shared memory in the
+// accumulator (split-FP32, ~2^-22 per product), or with Prob::split set the two small
+// products into a second accumulator (below). Operand stages sit in shared memory in the
 // canonical K-major no-swizzle layout (8-row x 16-byte core matrices); one thread issues
 // tcgen05.mma and commits to mbarriers; every wait is bounded and sets an error flag
 // instead of hanging; TMEM is drained with tcgen05.ld. Two forms:
@@ -17,6 +18,7 @@
 #pragma once
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include "transforms.cuh"
 
@@ -195,6 +197,15 @@ template <class P> struct BulkB<P, std::enable_if_t<P::kBulkB>> { static constex
 // Prob::kBulkA (persistent engine only): the A tiles are also in tables, Prob::a_tiles(z, r0, k0, hi, lo)
 template <class P, class = void> struct BulkA { static constexpr bool value = false; };
 template <class P> struct BulkA<P, std::enable_if_t<P::kBulkA>> { static constexpr bool value = true; };
+// Prob::split: hi*hi and the corrections in separate accumulators (both engine forms)
+template <class P, class = void> struct HasSplit { static constexpr bool value = false; };
+template <class P> struct HasSplit<P, std::void_t<decltype(std::declval<P>().split)>> {
+  static constexpr bool value = true;
+};
+template <class P> __host__ __device__ __forceinline__ bool split_of(const P& pb) {
+  if constexpr (HasSplit<P>::value) return pb.split;
+  else return false;
+}
 template <class Prob, int BN>
 __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   using G = Geo<BN>;
@@ -203,6 +214,10 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   const uint32_t raw = smem_u32(smraw);
   unsigned char* base = smraw + (((raw + 1023u) & ~1023u) - raw);  // 1024-byte aligned stage buffers
   constexpr bool BULK = BulkB<Prob>::value;
+  // with Prob::split the corrections go to a second accumulator BN columns on (the launch
+  // then keeps one CTA per SM, so that the two CTAs never wait for each other's TMEM)
+  const bool SA = split_of(pb);
+  const uint32_t TCOLS = SA ? 2 * G::TMEM_COLS : G::TMEM_COLS;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);  // MMAs of the stage done
   uint64_t* full = bars + STAGES;                                             // B copies of the stage landed
   uint64_t* drain = full + STAGES;                                            // all MMAs of the CTA done
@@ -223,7 +238,7 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(G::TMEM_COLS)
+                 "r"(TCOLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -309,9 +324,10 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
         const uint64_t ahi = smem_desc(sa + koff), alo = smem_desc(sa + A_BYTES + koff);
         const uint64_t bhi = smem_desc(sa + 2 * A_BYTES + koff), blo = smem_desc(sa + 2 * A_BYTES + B_BYTES + koff);
         const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
-        mma_tf32(tmem, alo, bhi, G::IDESC, first);
-        mma_tf32(tmem, ahi, blo, G::IDESC, 1u);
-        mma_tf32(tmem, ahi, bhi, G::IDESC, 1u);
+        const uint32_t acc_c = SA ? tmem + (uint32_t)BN : tmem;
+        mma_tf32(acc_c, alo, bhi, G::IDESC, first);
+        mma_tf32(acc_c, ahi, blo, G::IDESC, 1u);
+        mma_tf32(tmem, ahi, bhi, G::IDESC, SA ? first : 1u);
       }
       mma_commit(&bars[s]);
     }
@@ -346,6 +362,12 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
       if (nchunks > 0 && ok) {
         float d[16];
         tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cc, d);
+        if (SA) {
+          float e[16];
+          tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)BN + (uint32_t)cc, e);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) d[i] += e[i];
+        }
         pb.store16(mp, r0, c0g, r, cc, d);
       } else {
         pb.zero16(mp, r0, c0g, r, cc);
@@ -355,7 +377,7 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
   fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
   }
 }
 
@@ -374,6 +396,15 @@ __global__ void __launch_bounds__(NT, 2) tc_gemm_kernel(Prob pb, int* err) {
 //              to the stage's empty barrier, and after a tile's last chunk to acc_full;
 //   warps 18-21 drain the accumulator of the previous tile (two TMEM accumulators of BN
 //              columns alternate), then arrive on acc_empty.
+// Prob::split (a run-time flag of problems that have it): the two TMEM regions instead hold
+// one tile as a pair, the hi*hi products
+// in one and the hi*lo + lo*hi corrections in the other, which the epilogue adds. The
+// tensor core's FP32 accumulation behaves like truncation: each MMA step into the running
+// sum S loses about half an ulp of S, always towards zero, so the bias grows with the number
+// of steps at full magnitude. The corrections are ~2^-11 of S, so in their own accumulator
+// their steps cost almost nothing, and the full-size sum takes one step per K-step instead
+// of three (a third of the bias, measured on the analysis contraction). The price is that
+// the next tile's MMAs wait for the epilogue (one accumulator pair, not two alternating).
 // Every mbarrier wait is bounded and made by one lane whose result the warp shares, so
 // lanes never disagree; a role whose wait gives up records the error and stops, the others
 // then give up in turn, and B copies still in flight are waited for before the CTA exits.
@@ -409,6 +440,7 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
   using G = Geo<BN>;
   constexpr int B_BYTES = G::B_BYTES, STAGE_BYTES = G::STAGE_BYTES, S = WS_STAGES, D = WS_TRING;
   constexpr bool BA = BulkA<Prob>::value;
+  const bool SA = split_of(pb);
   constexpr int PW = WsWarps<Prob>::value, WS_WB = PW, WS_WM = PW + 1;
   static_assert(BulkB<Prob>::value, "the B operand comes from tables");
   static_assert(GeoWS<BN>::TMEM_COLS <= 512, "two accumulators fit in TMEM");
@@ -592,10 +624,12 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
         if (t >= ntiles) break;
         int mp, r0, c0, kb, nch;
         tile_of(t, mp, r0, c0, kb, nch);
-        const uint32_t a = j & 1u;
-        if (!mbar_wait(&acc_empty[a], ((j >> 1) + 1) & 1u, err)) break;
+        // the accumulator (pair) of tile j: alternating, or the one pair for every tile
+        const uint32_t a = SA ? 0u : (j & 1u), use = SA ? j : (j >> 1);
+        if (!mbar_wait(&acc_empty[a], (use + 1) & 1u, err)) break;
         fence_after();
         const uint32_t acc = tmem + a * (uint32_t)BN;
+        const uint32_t acc_c = SA ? tmem + (uint32_t)BN : acc;  // where hi*lo and lo*hi go
         for (int c = 0; c < nch; ++c, ++u) {
           const int s = u % S;
           if ((!BA && !mbar_wait(&a_full[s], (u / S) & 1u, err)) || !mbar_wait(&b_full[s], (u / S) & 1u, err)) {
@@ -609,9 +643,10 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
             const uint32_t koff = ks * 256;
             const uint64_t ahi = smem_desc(sa + koff), alo = smem_desc(sa + A_BYTES + koff);
             const uint64_t bhi = smem_desc(sa + 2 * A_BYTES + koff), blo = smem_desc(sa + 2 * A_BYTES + B_BYTES + koff);
-            mma_tf32(acc, alo, bhi, G::IDESC, (c == 0 && ks == 0) ? 0u : 1u);
-            mma_tf32(acc, ahi, blo, G::IDESC, 1u);
-            mma_tf32(acc, ahi, bhi, G::IDESC, 1u);
+            const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+            mma_tf32(acc_c, alo, bhi, G::IDESC, first);
+            mma_tf32(acc_c, ahi, blo, G::IDESC, 1u);
+            mma_tf32(acc, ahi, bhi, G::IDESC, SA ? first : 1u);
           }
           issued = true;
           mma_commit(&empty[s]);
@@ -630,13 +665,19 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
       if (!next_tile(j, t) || t >= ntiles) break;
       int mp, r0, c0, kb, nch;
       tile_of(t, mp, r0, c0, kb, nch);
-      const uint32_t a = j & 1u;
-      if (!warp_wait(&acc_full[a], (j >> 1) & 1u, err)) break;
+      const uint32_t a = SA ? 0u : (j & 1u), use = SA ? j : (j >> 1);
+      if (!warp_wait(&acc_full[a], use & 1u, err)) break;
       fence_after();
       for (int cc = 0; cc < BN; cc += 16) {
         if (nch > 0) {
           float d[16];
           tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + a * (uint32_t)BN + (uint32_t)cc, d);
+          if (SA) {
+            float e[16];
+            tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)BN + (uint32_t)cc, e);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) d[i] += e[i];
+          }
           pb.store16(mp, r0, c0, r, cc, d);
         } else {
           pb.zero16(mp, r0, c0, r, cc);
@@ -660,9 +701,16 @@ __global__ void __launch_bounds__((WsWarps<Prob>::value + 6) * 32, 1)
 
 template <class Prob, int BN>
 bool launch_tc_gemm(const Prob& pb, dim3 grid, int* err, cudaStream_t st, int kind) {
-  if (!func_attr_once((const void*)tc::tc_gemm_kernel<Prob, BN>, tc::Geo<BN>::SMEM_BYTES)) return false;
+  // a split accumulator takes all of TMEM: more than half of the SM's shared memory keeps a
+  // second CTA of the kernel off the SM
+  constexpr int smem_split = tc::Geo<BN>::SMEM_BYTES < 120 * 1024 ? 120 * 1024 : tc::Geo<BN>::SMEM_BYTES;
+  static_assert(!tc::HasSplit<Prob>::value || 2 * tc::Geo<BN>::TMEM_COLS <= 512, "the pair fits in TMEM");
+  const int smem = tc::split_of(pb) ? smem_split : tc::Geo<BN>::SMEM_BYTES;
+  if (!func_attr_once((const void*)tc::tc_gemm_kernel<Prob, BN>,
+                      tc::HasSplit<Prob>::value ? smem_split : tc::Geo<BN>::SMEM_BYTES))
+    return false;
   KTimer kt(kind, st);
-  tc::tc_gemm_kernel<Prob, BN><<<grid, tc::NT, tc::Geo<BN>::SMEM_BYTES, st>>>(pb, err);
+  tc::tc_gemm_kernel<Prob, BN><<<grid, tc::NT, smem, st>>>(pb, err);
   kt.done();
   return launch_ok(kind_name(kind));
 }
