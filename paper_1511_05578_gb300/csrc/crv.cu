@@ -267,9 +267,10 @@ struct crv_plan_s {
   double lambda = 2;
   bool real = false, mixed = false, wfp32 = false;
   bool unrot = false;  // coefficients of the unrotated curvelets (CRV_F_UNROTATED)
-  // unrotated plans: per scale, the smallest l >= |s| with kappa^(j)(l) > 0 (columns with
-  // |n| below it are zero, as are those with |m| > |n|) and the column pairs that are not
-  // zero, which are the only ones the beta transforms visit
+  // per scale, the smallest l >= |s| with kappa^(j)(l) > 0: Psi_ln = 0 below it, so the
+  // tensor-core K runs (analysis) and l-tiles (synthesis) start there; in unrotated plans
+  // also the columns with |n| below it are zero, as are those with |m| > |n|, and dpmap
+  // lists the column pairs that are not zero, the only ones the beta transforms visit
   std::vector<int> nlo;
   std::vector<int*> dpmap;
   std::vector<int> npmap;
@@ -1133,8 +1134,8 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
     for (int dir = 0; dir < 2; ++dir) {
       std::vector<int2> range;
       int ntiles = 0;
-      if (dir == 0) tc_analysis_ranges(Lb, cs, range, ntiles);
-      else tc_synthesis_ranges(Lb, cs, range, ntiles);
+      if (dir == 0) tc_analysis_ranges(Lb, p->nlo[j], cs, range, ntiles);
+      else tc_synthesis_ranges(Lb, p->nlo[j], cs, range, ntiles);
       std::vector<long long> base(range.size());
       long long total = 0;
       for (size_t i = 0; i < range.size(); ++i) {
@@ -1152,6 +1153,7 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
       TcTab t;
       t.hi = hi; t.lo = lo; t.base = dbase; t.range = drange; t.ntiles = ntiles;
       for (const int2& r : range) t.kmax = std::max(t.kmax, r.y);
+      t.lmin = p->nlo[j];
       const bool ok = dir == 0 ? tc_fill_analysis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st)
                                : tc_fill_synthesis_table(p->dQ32, p->L, p->dpsi32[j], Lb, cs, t, hi, lo, st);
       if (!ok) return CRV_ECUDA;
@@ -1165,7 +1167,7 @@ static int build_tc_tables(crv_plan_s* p, cudaStream_t st) {
     const ColSet cs = p->colset(p->Lj[j]);
     std::vector<int2> range;
     int nmt = 0;
-    tc_analysis_a_ranges(p->Lj[j], cs, range, nmt);
+    tc_analysis_a_ranges(p->Lj[j], p->nlo[j], cs, range, nmt);
     std::vector<long long> base(range.size());
     long long total = 0;
     for (size_t i = 0; i < range.size(); ++i) {

@@ -160,18 +160,19 @@ struct SynthesisProb {
 };
 
 // f_lm += sum_{m' <= l} Delta^l_{m'm} Z[m'][mi][l] (Eq. flml's sum over m'), one thread per
-// (l, m), threads of a block along l (Z reads coalesced). Delta^l_{m'm} is read as
+// (l, m) with l >= lmin (below the kernel's support Z is zero and its tiles are not
+// computed), threads of a block along l (Z reads coalesced). Delta^l_{m'm} is read as
 // Delta^l_{|m| m'} from the FP32 table, contiguous in m' for each thread: with
 // Delta^l_{m'm} = (-1)^{m'-m} Delta^l_{mm'} and Delta^l_{m',-n} = (-1)^{l+m'} Delta^l_{m'n},
 //   m >= 0: Delta^l_{m'm} = (-1)^{m'+m} Q[m][l][m'],   m < 0: (-1)^{l+|m|} Q[|m|][l][m'].
 // Products and partial sums in FP32, flushed into an FP64 accumulator every 32 terms;
 // f_lm accumulates in FP64.
 __global__ void __launch_bounds__(256) synth_reduce_kernel(const float* __restrict__ Q32, int Lmax,
-                                                          const cx<float>* __restrict__ Z, int Lb, ColSet cs,
-                                                          cx<double>* __restrict__ flm) {
+                                                          const cx<float>* __restrict__ Z, int Lb, int lmin,
+                                                          ColSet cs, cx<double>* __restrict__ flm) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x, mi = blockIdx.y;
   const int m = cs.m0 + mi, am = m < 0 ? -m : m;
-  if (l >= Lb || am > l) return;
+  if (l >= Lb || l < lmin || am > l) return;
   const float* __restrict__ q = Q32 + ((size_t)am * Lmax + l) * Lmax;  // q[m'] = Delta^l_{|m| m'}
   const cx<float>* __restrict__ z = Z + (size_t)mi * Lb + l;           // z[m' * Mc * Lb]
   const size_t zs = (size_t)cs.Mc * Lb;
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(TC_A_ROWS) fill_analysis_a_kernel(const float*
 // ---------------------------------------------------------------------------
 // Host entry points used by crv.cu
 // ---------------------------------------------------------------------------
-void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
+void tc_analysis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
   ntiles = (cs.Nc + TC_TILE_ROWS - 1) / TC_TILE_ROWS;
   const int nchunk = (Lb + TC_CHUNK_K - 1) / TC_CHUNK_K;
   range.assign((size_t)Lb * ntiles, make_int2(0, 0));
@@ -310,13 +311,13 @@ void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int&
       const int nlo = cs.n0 + cs.nstep * (t * TC_TILE_ROWS);
       const int nhi = cs.n0 + cs.nstep * (std::min((t + 1) * TC_TILE_ROWS, cs.Nc) - 1);
       const int bmin = (nlo <= 0 && nhi >= 0) ? 0 : std::min(std::abs(nlo), std::abs(nhi));
-      const int kb = std::max(mp, bmin);
+      const int kb = std::max(std::max(mp, bmin), lmin);  // B rows l < lmin are zero
       if (kb >= Lb) continue;
       range[(size_t)mp * ntiles + t] = make_int2(kb / TC_CHUNK_K, nchunk - kb / TC_CHUNK_K);
     }
 }
 
-void tc_analysis_a_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& nmt) {
+void tc_analysis_a_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& nmt) {
   nmt = (cs.Mc + TC_A_ROWS / 2 - 1) / (TC_A_ROWS / 2);
   const int nchunk = (Lb + TC_CHUNK_K - 1) / TC_CHUNK_K;
   range.assign((size_t)Lb * nmt, make_int2(0, 0));
@@ -324,19 +325,20 @@ void tc_analysis_a_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, in
     for (int t = 0; t < nmt; ++t) {
       const int mlo = cs.m0 + t * (TC_A_ROWS / 2), mhi = cs.m0 + std::min((t + 1) * (TC_A_ROWS / 2), cs.Mc) - 1;
       const int amin = (mlo <= 0 && mhi >= 0) ? 0 : std::min(std::abs(mlo), std::abs(mhi));
-      const int kb = std::max(mp, amin);
+      // the same lower limits as the B runs, so every chunk a tile visits is in its A run
+      const int kb = std::max(std::max(mp, amin), lmin);
       if (kb >= Lb) continue;
       range[(size_t)mp * nmt + t] = make_int2(kb / TC_CHUNK_K, nchunk - kb / TC_CHUNK_K);
     }
 }
 
-void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
+void tc_synthesis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& ntiles) {
   ntiles = (Lb + TC_TILE_ROWS - 1) / TC_TILE_ROWS;
   range.assign((size_t)Lb * ntiles, make_int2(0, 0));
   for (int mp = 0; mp < Lb; ++mp)
     for (int t = 0; t < ntiles; ++t) {
       const int lhi = std::min((t + 1) * TC_TILE_ROWS, Lb) - 1;
-      if (mp > lhi) continue;
+      if (mp > lhi || lhi < lmin) continue;  // every row l of the tile below the support: Z = 0
       const int d = -lhi - cs.n0, dmax = lhi - cs.n0;
       const int kb = d <= 0 ? 0 : (d + cs.nstep - 1) / cs.nstep;
       const int ke = dmax < 0 ? 0 : std::min(cs.Nc, dmax / cs.nstep + 1);
@@ -407,7 +409,7 @@ bool tc_synthesis(const float* Q32, int Lmax, const cx<float>* Y, TcTab tb, int 
   if (!ok) return false;
   dim3 g2((Lb + 255) / 256, cs.Mc);
   KTimer kt(K_TC_S, st);
-  tc::synth_reduce_kernel<<<g2, 256, 0, st>>>(Q32, Lmax, Zscratch, Lb, cs, flm);
+  tc::synth_reduce_kernel<<<g2, 256, 0, st>>>(Q32, Lmax, Zscratch, Lb, tb.lmin, cs, flm);
   kt.done();
   return launch_ok("synth_reduce_kernel");
 }

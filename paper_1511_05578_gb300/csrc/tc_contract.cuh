@@ -24,6 +24,7 @@ struct TcTab {
   const int2* range = nullptr;
   int ntiles = 0;
   int kmax = 0;  // the longest run of K chunks over (m', tile)
+  int lmin = 0;  // first l of the scale's kernel support (Psi_ln = 0 below it)
 };
 constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 16, TC_CHUNK_FLOATS = TC_TILE_ROWS * TC_CHUNK_K;
 // The tensor core's FP32 accumulation behaves like truncation, so the error of a long K sum
@@ -48,10 +49,10 @@ struct TcATab {
 };
 
 // Chunk ranges per (m', tile), m' < Lb (host).
-void tc_analysis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
+void tc_analysis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& ntiles);
 // Chunk ranges of the per-map A tables per (m', m-tile) (host).
-void tc_analysis_a_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& nmt);
-void tc_synthesis_ranges(int Lb, const ColSet& cs, std::vector<int2>& range, int& ntiles);
+void tc_analysis_a_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& nmt);
+void tc_synthesis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& ntiles);
 // Fill a table (device); t.base / t.range already on the device.
 bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
                             float* lo, cudaStream_t st);
