@@ -183,6 +183,19 @@ int crv_plan_check_guards(crv_plan_t plan, int* nbad);
 int crv_plan_guard_count(crv_plan_t plan, int* n);
 int crv_debug_poke_guard(crv_plan_t plan, int which);
 
+/* Host check of the K runs of the tensor-core contractions (no counterpart in the paper; runs
+ * on the host only, no device work). For one scale of band limit Lb (1 <= Lb <= 1024) and the
+ * column set of a real spin-0 signal (real != 0) or a complex spin-`spin` one, rotated or
+ * unrotated (unrot != 0), it builds the runs as a plan does: analysis B runs and synthesis
+ * l-tiles from l = lmin_b, analysis A runs from l = lmin_a (a plan passes the first l of the
+ * scale's kernel support as both; 0 <= lmin <= Lb). It counts the tiles that break the
+ * engines' rules: an analysis tile whose K chunks leave its B or A run, or miss an l >= lmin_b
+ * that its products need; a synthesis tile whose output the reduction over m' reads, with no
+ * K chunks or with chunks missing an n it needs. *bad gets that count (0: consistent), *tiles
+ * (if not NULL) the number of tiles checked. CRV_EINVAL for a bad argument. */
+int crv_debug_check_tc_ranges(int Lb, int lmin_b, int lmin_a, int real, int spin, int unrot, long long* tiles,
+                              long long* bad);
+
 /* Host copy of plan tables, for inspection and tests.
  *   crv_plan_kernel:  psi[l][n + L_j - 1] = sPsi^(j)_ln (real, Eq. wav_factorized), l < L_j
  *   crv_plan_scaling: phi[l] = sqrt(4pi/(2l+1)) Phi_l0 = sqrt(k_lambda(l/lambda^J0)), l < L

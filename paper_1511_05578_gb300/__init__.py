@@ -14,7 +14,7 @@ import os
 
 __all__ = [
     "CRV_OK", "CRV_EINVAL", "CRV_ENOMEM", "CRV_ECUDA", "CRV_ETIMEOUT", "CRV_EUNSUPPORTED", "CRV_EGUARD", "CRV_F_GUARD",
-    "crv_plan_check_guards", "crv_plan_guard_count", "crv_debug_poke_guard",
+    "crv_plan_check_guards", "crv_plan_guard_count", "crv_debug_poke_guard", "crv_debug_check_tc_ranges",
     "CRV_NRULE_CURVELET", "CRV_F_REAL", "CRV_F_MIXED", "CRV_F_W_FP32", "CRV_F_UNROTATED", "CRV_F_TUNE", "CRV_F_FP64_TC", "CrvError",
     "lib_path", "load", "crv_plan_create", "crv_plan_destroy", "crv_plan_clone", "crv_plan_bytes", "crv_plan_tuning", "crv_plan_info", "crv_plan_check", "crv_plan_check_stream", "crv_debug_bounded_wait", "crv_plan_kernel",
     "crv_plan_scaling", "crv_plan_delta", "crv_sht_fwd", "crv_sht_inv", "crv_analysis",
@@ -65,6 +65,8 @@ def load():
         "crv_plan_check_guards": (i, [vp, ctypes.POINTER(i)]),
         "crv_plan_guard_count": (i, [vp, ctypes.POINTER(i)]),
         "crv_debug_poke_guard": (i, [vp, i]),
+        "crv_debug_check_tc_ranges": (i, [i, i, i, i, i, i, ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_longlong)]),
         "crv_plan_kernel": (i, [vp, i, ctypes.POINTER(d)]),
         "crv_plan_scaling": (i, [vp, ctypes.POINTER(d)]),
         "crv_plan_delta": (i, [vp, i, ctypes.POINTER(d)]),
@@ -244,6 +246,14 @@ def crv_plan_guard_count(plan):
 def crv_debug_poke_guard(plan, which):
     """Change one byte inside guard region `which` (tests the check itself)."""
     _check(load().crv_debug_poke_guard(plan, int(which)))
+
+
+def crv_debug_check_tc_ranges(Lb, lmin_b, lmin_a, real, spin=0, unrot=False):
+    """(tiles that break the tensor-core engines' run rules, tiles checked) for one scale; host only."""
+    tiles, bad = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(load().crv_debug_check_tc_ranges(int(Lb), int(lmin_b), int(lmin_a), int(bool(real)), int(spin),
+                                            int(bool(unrot)), ctypes.byref(tiles), ctypes.byref(bad)))
+    return bad.value, tiles.value
 
 
 def crv_plan_kernel(plan, j, out):

@@ -261,6 +261,22 @@ struct TableSet {
   }
 };
 
+// The (m, n) column set of a scale of band limit Lb: m >= 0 only for real signals (conjugate
+// symmetry); even n only for rotated spin-0 curvelets (zeta_lk = 0 for odd k at vartheta =
+// pi/2), while the unrotated ones sit at n = +-l, which covers every n.
+static ColSet colset_for(int Lb, bool real, int spin, bool unrot) {
+  ColSet c;
+  c.Mc = real ? Lb : 2 * Lb - 1;
+  c.m0 = real ? 0 : -(Lb - 1);
+  c.nstep = (spin == 0 && !unrot) ? 2 : 1;
+  c.n0 = -(Lb - 1);
+  if (c.nstep == 2 && (c.n0 & 1)) c.n0 += 1;
+  c.Nc = (-c.n0 - c.n0) / c.nstep + 1;
+  c.extra = 0;
+  c.fNc = FastDiv((uint32_t)c.Nc);
+  return c;
+}
+
 struct crv_plan_s {
   int L = 0, J0 = 0, J = 0, spin = 0, max_batch = 0, Lphi = 1;
   unsigned flags = 0;
@@ -382,23 +398,12 @@ struct crv_plan_s {
     if (fork_ev) cudaEventDestroy(fork_ev);
     for (void* p : allocs) cudaFree(p);
   }
-  int mc(int Lb) const { return real ? Lb : 2 * Lb - 1; }
-  int m0(int Lb) const { return real ? 0 : -(Lb - 1); }
-  // n-set: spin 0 rotated curvelets have zeta_lk = 0 for odd k (vartheta = pi/2); the
-  // unrotated ones sit at n = +-l, which covers every n
-  int nstep() const { return (spin == 0 && !unrot) ? 2 : 1; }
-  int n0(int Lb) const {
-    if (nstep() == 1) return -(Lb - 1);
-    int n = -(Lb - 1);
-    if (n & 1) n += 1;
-    return n;
-  }
-  int nc(int Lb) const { return (-n0(Lb) - n0(Lb)) / nstep() + 1; }
-  ColSet colset(int Lb) const {
-    ColSet c; c.Mc = mc(Lb); c.m0 = m0(Lb); c.Nc = nc(Lb); c.n0 = n0(Lb); c.nstep = nstep(); c.extra = 0;
-    c.fNc = FastDiv((uint32_t)c.Nc);
-    return c;
-  }
+  ColSet colset(int Lb) const { return colset_for(Lb, real, spin, unrot); }
+  int mc(int Lb) const { return colset(Lb).Mc; }
+  int m0(int Lb) const { return colset(Lb).m0; }
+  int nstep() const { return colset(1).nstep; }
+  int n0(int Lb) const { return colset(Lb).n0; }
+  int nc(int Lb) const { return colset(Lb).Nc; }
 };
 
 // The A table of pass [cuts[i], cuts[i + 1]) of a per-map A layout, in the plan's buffer.
@@ -1829,6 +1834,16 @@ int crv_plan_check_guards(crv_plan_t p, int* nbad) {
   }
   if (nbad) *nbad = bad;
   if (bad) return fail(CRV_EGUARD, std::to_string(bad) + " guard region(s) written: " + first);
+  return CRV_OK;
+}
+
+int crv_debug_check_tc_ranges(int Lb, int lmin_b, int lmin_a, int real, int spin, int unrot, long long* tiles,
+                              long long* bad) {
+  if (!bad) return fail(CRV_EINVAL, "bad is NULL");
+  if (Lb < 1 || Lb > 1024) return fail(CRV_EINVAL, "Lb must be in [1, 1024]");
+  if (lmin_b < 0 || lmin_b > Lb || lmin_a < 0 || lmin_a > Lb) return fail(CRV_EINVAL, "lmin must be in [0, Lb]");
+  if (real && spin != 0) return fail(CRV_EINVAL, "real signals have spin 0");
+  *bad = tc_check_ranges(Lb, lmin_b, lmin_a, colset_for(Lb, real != 0, spin, unrot != 0), tiles);
   return CRV_OK;
 }
 

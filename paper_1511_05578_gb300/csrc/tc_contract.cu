@@ -41,12 +41,9 @@ struct AnalysisProb {
   // K chunks: the table's run for (m', n-tile), skipping chunks below min |m| of the m-tile
   __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& n0i, int& kb, int& ke) const {
     mp = bz; mi0 = by * (BM / 2); n0i = bx * BNC;
-    const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
-    const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
-    const int2 rg = tb.range[mp * tb.ntiles + bx];
-    const int c0 = max(rg.x, amin / TC_CHUNK_K), c1 = rg.x + rg.y;
-    kb = c0 * TC_CHUNK_K;
-    ke = max(c0, c1) * TC_CHUNK_K;
+    const int2 ch = tc_analysis_tile_chunks(tb.range[mp * tb.ntiles + bx], tc_tile_amin(cs, mi0, BM / 2));
+    kb = ch.x * TC_CHUNK_K;
+    ke = ch.y * TC_CHUNK_K;
   }
   // A chunk: row r = 2 (m - mi0) + (re|im), k-quad q of chunk starting at k0
   __device__ void a4(int mp, int mi0, int k0, int r, int q, float* x) const {
@@ -116,8 +113,7 @@ struct SynthesisProb {
   __device__ void tile(int bx, int by, int bz, int& mp, int& mi0, int& l0, int& kb, int& ke) const {
     mp = bz; mi0 = by * (BM / 2); l0 = bx * BNC;
     const int2 rg = tb.range[mp * tb.ntiles + bx];
-    const int mlo = cs.m0 + mi0, mhi = cs.m0 + min(mi0 + BM / 2, cs.Mc) - 1;
-    const int amin = (mlo <= 0 && mhi >= 0) ? 0 : min(abs(mlo), abs(mhi));
+    const int amin = tc_tile_amin(cs, mi0, BM / 2);
     const int lhi = min(l0 + BNC, Lb) - 1;
     kb = rg.x * TC_CHUNK_K;
     ke = amin > lhi ? kb : (rg.x + rg.y) * TC_CHUNK_K;
@@ -323,8 +319,7 @@ void tc_analysis_a_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>&
   range.assign((size_t)Lb * nmt, make_int2(0, 0));
   for (int mp = 0; mp < Lb; ++mp)
     for (int t = 0; t < nmt; ++t) {
-      const int mlo = cs.m0 + t * (TC_A_ROWS / 2), mhi = cs.m0 + std::min((t + 1) * (TC_A_ROWS / 2), cs.Mc) - 1;
-      const int amin = (mlo <= 0 && mhi >= 0) ? 0 : std::min(std::abs(mlo), std::abs(mhi));
+      const int amin = tc_tile_amin(cs, t * (TC_A_ROWS / 2), TC_A_ROWS / 2);
       // the same lower limits as the B runs, so every chunk a tile visits is in its A run
       const int kb = std::max(std::max(mp, amin), lmin);
       if (kb >= Lb) continue;
@@ -346,6 +341,57 @@ void tc_synthesis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& 
       const int c0 = kb / TC_CHUNK_K, c1 = (ke + TC_CHUNK_K - 1) / TC_CHUNK_K;
       range[(size_t)mp * ntiles + t] = make_int2(c0, c1 - c0);
     }
+}
+
+long long tc_check_ranges(int Lb, int lmin_b, int lmin_a, const ColSet& cs, long long* tiles) {
+  static_assert(TC_A_ROWS == tc::BM && TC_TILE_ROWS == tc::BNC, "table tiles are engine tiles");
+  std::vector<int2> rb, ra, rs;
+  int nt = 0, nmt = 0, nts = 0;
+  tc_analysis_ranges(Lb, lmin_b, cs, rb, nt);
+  tc_analysis_a_ranges(Lb, lmin_a, cs, ra, nmt);
+  tc_synthesis_ranges(Lb, lmin_b, cs, rs, nts);
+  const int nchunk = (Lb + TC_CHUNK_K - 1) / TC_CHUNK_K, MR = TC_A_ROWS / 2;
+  long long bad = 0, n = 0;
+  for (int mp = 0; mp < Lb; ++mp)
+    for (int by = 0; by < nmt; ++by) {
+      const int amin = tc_tile_amin(cs, by * MR, MR);
+      const int2 a = ra[(size_t)mp * nmt + by];
+      for (int bx = 0; bx < nt; ++bx) {  // analysis: rows (m, Re|Im), columns n, K = l
+        ++n;
+        const int2 rg = rb[(size_t)mp * nt + bx];
+        const int2 ch = tc_analysis_tile_chunks(rg, amin);
+        const int nlo = cs.n0 + cs.nstep * (bx * TC_TILE_ROWS);
+        const int nhi = cs.n0 + cs.nstep * (std::min((bx + 1) * TC_TILE_ROWS, cs.Nc) - 1);
+        const int bmin = (nlo <= 0 && nhi >= 0) ? 0 : std::min(std::abs(nlo), std::abs(nhi));
+        // lowest l of a nonzero product: l >= m', l >= |m|, l >= |n| and Psi_ln != 0
+        const int need = std::max(std::max(mp, lmin_b), std::max(amin, bmin));
+        bool ok = true;
+        if (ch.y > ch.x) {
+          ok = rg.x <= ch.x && ch.y <= rg.x + rg.y && ch.y <= nchunk && a.y > 0 && a.x <= ch.x &&
+               ch.y <= a.x + a.y;
+        }
+        if (need < Lb) ok = ok && ch.y > ch.x && ch.x * TC_CHUNK_K <= need && ch.y == nchunk;
+        if (!ok) ++bad;
+      }
+      for (int bx = 0; bx < nts; ++bx) {  // synthesis: rows (m, Re|Im), columns l, K = n
+        ++n;
+        const int2 rg = rs[(size_t)mp * nts + bx];
+        const int llo = bx * TC_TILE_ROWS, lhi = std::min(llo + TC_TILE_ROWS, Lb) - 1;
+        const bool work = !(amin > lhi) && rg.y > 0;  // the rule of SynthesisProb::tile
+        // the reduction reads Z[m'][m][l] for l >= max(lmin, m', |m|)
+        const bool read = std::max(std::max(lmin_b, llo), std::max(mp, amin)) <= lhi;
+        bool ok = !read || work;
+        if (read && work) {  // every n with |n| <= lhi inside the run
+          const int d = -lhi - cs.n0, dmax = lhi - cs.n0;
+          const int kb = d <= 0 ? 0 : (d + cs.nstep - 1) / cs.nstep;
+          const int ke = dmax < 0 ? 0 : std::min(cs.Nc, dmax / cs.nstep + 1);
+          ok = rg.x * TC_CHUNK_K <= kb && ke <= (rg.x + rg.y) * TC_CHUNK_K;
+        }
+        if (!ok) ++bad;
+      }
+    }
+  if (tiles) *tiles = n;
+  return bad;
 }
 
 bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,

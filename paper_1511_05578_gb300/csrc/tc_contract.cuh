@@ -34,6 +34,19 @@ constexpr int TC_TILE_ROWS = 256, TC_CHUNK_K = 16, TC_CHUNK_FLOATS = TC_TILE_ROW
 // buffered accumulator pair; the shorter runs stay double-buffered.
 constexpr int TC_SPLIT_K = 512;
 
+// Smallest |m| over the tile of `rows` values of m from column index mi0 (0 if it holds m = 0).
+__host__ __device__ inline int tc_tile_amin(const ColSet& cs, int mi0, int rows) {
+  const int mlo = cs.m0 + mi0, mend = mi0 + rows < cs.Mc ? mi0 + rows : cs.Mc, mhi = cs.m0 + mend - 1;
+  const int alo = mlo < 0 ? -mlo : mlo, ahi = mhi < 0 ? -mhi : mhi;
+  return (mlo <= 0 && mhi >= 0) ? 0 : (alo < ahi ? alo : ahi);
+}
+// K chunks [x, y) that an analysis tile multiplies: its B run rg from the m-tile's smallest |m|
+// on (Delta^l_{m'm} = 0 for l < |m|); empty (x == y) when that lies past the run.
+__host__ __device__ inline int2 tc_analysis_tile_chunks(int2 rg, int amin) {
+  const int c0 = rg.x > amin / TC_CHUNK_K ? rg.x : amin / TC_CHUNK_K, c1 = rg.x + rg.y;
+  return make_int2(c0, c1 > c0 ? c1 : c0);
+}
+
 // Per-map A operand of the analysis contraction for one scale (rebuilt for every map and
 // scale): for every (m', m-tile of 64 values of m) the run of 16-wide K chunks from
 // l = max(m', min |m| of the tile) on, each chunk a 128-row x 16 block (rows (m, Re|Im),
@@ -53,6 +66,12 @@ void tc_analysis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& r
 // Chunk ranges of the per-map A tables per (m', m-tile) (host).
 void tc_analysis_a_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& nmt);
 void tc_synthesis_ranges(int Lb, int lmin, const ColSet& cs, std::vector<int2>& range, int& ntiles);
+// Host check of one scale's runs as the plan builds them (B runs from lmin_b, A runs from
+// lmin_a; a plan uses one lmin for both) against the engines' tile rules: every analysis tile
+// with work stays inside its B and A runs and covers every l >= lmin_b its products need,
+// and every synthesis tile whose Z the m' reduction reads has work covering its n. Returns the
+// number of tiles that break a rule; *tiles gets the number checked.
+long long tc_check_ranges(int Lb, int lmin_b, int lmin_a, const ColSet& cs, long long* tiles);
 // Fill a table (device); t.base / t.range already on the device.
 bool tc_fill_analysis_table(const float* Q32, int Lmax, const float* psi, int Lb, ColSet cs, TcTab t, float* hi,
                             float* lo, cudaStream_t st);
