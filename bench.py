@@ -146,10 +146,19 @@ def plan_shapes(L, lam, J0, real=True, spin=0, unrot=False):
     return J, out
 
 
-def contraction_terms(Lb, real=True, spin=0):
-    """Number of (l, m, n, m'>=0) terms of the Delta contraction of one scale."""
+def support_start(lam, j):
+    """First l with kappa^(j)(l) > 0: the smallest integer above lam^(j-1) (kappa^(j) vanishes
+    for l <= lam^(j-1), where both k_lambda arguments are at most 1/lam)."""
+    v = lam ** (j - 1)
+    r = round(v)
+    return (int(r) if abs(v - r) < 1e-9 * max(1, v) else int(math.floor(v))) + 1
+
+
+def contraction_terms(Lb, lmin=0, real=True, spin=0):
+    """Number of (l, m, n, m'>=0) terms of the Delta contraction of one scale, over the l of the
+    kernel's support (l >= lmin; Psi_ln = 0 below it)."""
     tot = 0
-    for l in range(Lb):
+    for l in range(lmin, Lb):
         nm = (l + 1) if real else (2 * l + 1)       # m in the m-set with |m| <= l
         nn = 2 * (l // 2) + 1 if spin == 0 else 2 * l + 1  # even n (spin 0) with |n| <= l
         tot += (l + 1) * nm * nn                     # m' = 0..l
@@ -175,7 +184,7 @@ def kind_work(L, lam, J0, el_bytes, w_bytes, unrot=False):
     for (j, Lb, N, Mc, Nc) in shapes:
         vol = Lb * Mc * Nc * el_bytes           # X, Xb, Y volumes (complex)
         wv = Lb * N * N * w_bytes               # W_j
-        terms = contraction_terms(Lb)
+        terms = contraction_terms(Lb, support_start(lam, j))
         Q = 1 << max(3, (4 * Lb - 4).bit_length())
         if unrot:
             # single term l = |n|: the volume is written (analysis) or read (synthesis) once
